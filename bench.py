@@ -1,0 +1,417 @@
+"""Benchmark: 6-D cell-updates per second of one Strang step of the CHASM scheme on GB300.
+
+Workload (default): hydrogen 1s stationarity, V = -1/|x|, grid 32^3 x 32^3 on [-12,12]^3 x
+[-4,4)^3 (1.07e9 cells), dt = 0.025, initial f = the 1s Wigner function (discrete Fourier sum,
+N_y = 128) written on the GPU.  The headline `value` is the FP32-mixed form; the FP64 form is
+measured on the same GPU and reported under "fp64".
+
+Prints ONE JSON line (rank 0).  Under torchrun with N > 1 every rank runs its own replica of the
+workload on its own GPU (no data-path collective) and `value` is the sum over ranks of cells
+updated divided by the slowest rank's time ("scaling": "weak").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl chasm|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "6-D cell-updates/s per Strang step, FP32-mixed vs FP64 at stated L2 error"
+UNIT = "cell-updates/s"
+
+WORKLOAD = {
+    "name": "hydrogen-1s 32^3x32^3 [-12,12]^3 x [-4,4)^3, V=-1/|x|, dt=0.025",
+    "nx": 32, "nk": 32, "L": 12.0, "lk": 4.0, "dt": 0.025,
+    "nuclei": [((0.0, 0.0, 0.0), 1.0)], "n_y": 128,
+}
+
+
+# ------------------------------------------------------------------------------------------------
+# algorithmic work of the dominant kernel (the Theta kernel, one launch = one Horner stage)
+def theta_flops_per_cell(nk: int) -> float:
+    """Per cell and nucleus: 14 N^2 padded length-2N complex FFTs at 5 L log2 L flops
+    (L = 2N), the symbol multiply 2 (2N)^3, modulation 2 N^3 and demodulation/Im/scale 4 N^3,
+    all divided by N^3."""
+    L = 2 * nk
+    fft = 14 * nk * nk * 5 * L * math.log2(L)
+    return (fft + 2 * L ** 3 + 6 * nk ** 3) / nk ** 3
+
+
+def fp32_alu_peak_tflops() -> float:
+    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x the maximum SM clock."""
+    mhz = 2070.0
+    try:
+        mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+    except Exception:
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def theta_source_hash() -> str:
+    p = os.path.join(ROOT, "paper_2205_02380_gb300", "csrc", "k_theta.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the Theta kernel from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "theta_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("k_theta_sha256_16") != theta_source_hash():
+        return None
+    return d
+
+
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+def make_solver(ch, precision, stream):
+    W = WORKLOAD
+    return ch.Solver(W["nx"], W["nk"], -W["L"], W["L"], W["lk"], nuclei=W["nuclei"],
+                     precision=precision, stream=stream.cuda_stream)
+
+
+def time_steps(torch, s, f, dt, steps, warmup, stream, dist):
+    """W untimed steps, then exactly `steps` Strang steps between CUDA events on the solver's
+    stream, bracketed by barrier + synchronize.  Returns milliseconds."""
+    s.step(f, dt, warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(f, dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def time_theta_launches(torch, s, f, stream, reps):
+    """Average duration of one launch of the Theta kernel (chasm_theta = exactly one launch)."""
+    out = torch.empty_like(f)
+    s.theta(f, out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        s.theta(f, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    del out
+    return e0.elapsed_time(e1) / reps
+
+
+def cpu_baseline(seconds_target: float = 20.0):
+    """Runs the FP64 oracle on a bounded sample of the workload in a fresh single-threaded
+    process and returns its throughput (see oracle_sample)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                        "--sample-seconds", str(seconds_target)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample(seconds_target: float) -> dict:
+    """Times the oracle's three substeps on pieces of the full-size workload:
+    A(dt/2) on the full 32^3 x-cube at n_k sampled k points (the spline transform and the
+    64-tap sum are independent per k), and P(dt) (four Theta^T applications) at n_x sampled x
+    points (independent per x point).  Cell-update time = 2 t_A + t_P per cell."""
+    import numpy as np
+
+    import synth
+    from oracle import chasm_oracle as O
+    W = WORKLOAD
+    nx, nk, L, lk, dt = W["nx"], W["nk"], W["L"], W["lk"], W["dt"]
+    prob = O.Problem(nx=(nx,) * 3, nk=nk, x_lo=(-L,) * 3, x_hi=(L,) * 3, lk=lk,
+                     nuclei=W["nuclei"])
+    ks = prob.ks()
+    # A: n_kA k points on the full x cube (surrogate smooth data; the cost is data independent)
+    xs = prob.xs(0)
+    g = np.exp(-0.5 * xs ** 2)
+    n_kA = 2
+    kidx = [(3, 17, 29), (20, 8, 14)][:n_kA]
+    cube = (g[:, None, None] * g[None, :, None] * g[None, None, :])[..., None, None, None]
+    t0 = time.perf_counter()
+    for (a, b, c) in kidx:
+        O.advect(cube, prob, 0.5 * dt, kaxes=(ks[a:a + 1], ks[b:b + 1], ks[c:c + 1]))
+    tA = (time.perf_counter() - t0) / (n_kA * nx ** 3)
+    # P: x points with the 1s data
+    T = O.tkm_tensor(nk, lk)
+    xpts = []
+    tP_total, n_xP = 0.0, 0
+    rng = np.random.default_rng(2205)
+    while n_xP < 2 or tP_total < seconds_target * 0.5:
+        i = rng.integers(0, nx, 3)
+        x = np.array([xs[i[0]], xs[i[1]], xs[i[2]]])
+        f1 = synth.wigner_1s((2, 2, 2), nk, tuple(x), tuple(x + 1.0), lk, n_y=W["n_y"])[:1, :1, :1]
+        t0 = time.perf_counter()
+        O.pflow_coulomb(f1.reshape(1, nk, nk, nk), prob, dt, T, xpts=x[None])
+        tP_total += time.perf_counter() - t0
+        n_xP += 1
+        xpts.append(x)
+        if n_xP >= 16:
+            break
+    tP = tP_total / (n_xP * nk ** 3)
+    t_cell = 2 * tA + tP
+    return {"value": 1.0 / t_cell, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, 1 thread: A(dt/2) on the full 32^3 x-cube at {n_kA} "
+                      f"k points ({tA * 1e6:.2f} us/cell) and P(dt) on {n_xP} x points of the 1s "
+                      f"data ({tP * 1e6:.2f} us/cell); cell-update time = 2 t_A + t_P"}
+
+
+# ------------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle_sample(max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+        if i >= args.warmup:
+            per_step.append(r["value"])
+    value = statistics.median(per_step)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "cells": WORKLOAD["nx"] ** 3 * WORKLOAD["nk"] ** 3,
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_chasm(args):
+    import torch
+    import paper_2205_02380_gb300 as ch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    ch.chasm.lib()
+    W = WORKLOAD
+    cells = W["nx"] ** 3 * W["nk"] ** 3
+    dt = W["dt"]
+    stream = torch.cuda.Stream()
+    result = {}
+    # baseline of the host cores first (no CUDA state is shared with the child process)
+    base = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+
+    sampler = ClockSampler(local)
+    for prec_name, prec, steps in (("fp32", ch.FP32_MIXED, args.steps),
+                                   ("fp64", ch.FP64, max(1, min(args.steps, args.fp64_steps)))):
+        with torch.cuda.stream(stream):
+            s = make_solver(ch, prec, stream)
+            dtp = torch.float32 if prec == ch.FP32_MIXED else torch.float64
+            f = torch.empty((W["nx"],) * 3 + (W["nk"],) * 3, device="cuda", dtype=dtp)
+            s.init_hydrogen_1s(f, n_y=W["n_y"])
+            m0, e0 = s.moments(f)
+            if prec_name == "fp32":
+                sampler.start()
+            ms = time_steps(torch, s, f, dt, steps, args.warmup if prec_name == "fp32" else 1,
+                            stream, dist)
+            if prec_name == "fp32":
+                clocks = sampler.stop()
+            m1, e1 = s.moments(f)
+            ms_t = ms
+            if dist:
+                t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                ms_t = float(t.item())
+            entry = {"ms_per_step": ms_t / steps, "steps": steps,
+                     "value": world * cells * steps / (ms_t / 1e3),
+                     "mass0": m0, "mass": m1, "energy0": e0, "energy": e1}
+            if prec_name == "fp32":
+                reps = 5
+                entry["theta_ms"] = time_theta_launches(torch, s, f, stream, reps)
+                # end-to-end through the C ABI with HOST buffers (pinned), copies included
+                host = torch.empty(f.shape, dtype=dtp, pin_memory=True)
+                host.copy_(f.cpu())
+                hout = torch.empty_like(host, pin_memory=True)
+                k_e2e = max(1, min(steps, args.e2e_steps))
+                s.run_host(host.data_ptr(), hout.data_ptr(), dt, 1)   # warm: buffer + graph
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.run_host(host.data_ptr(), hout.data_ptr(), dt, k_e2e)
+                t_e2e = time.perf_counter() - t0
+                entry["e2e"] = {"value": world * cells * k_e2e / t_e2e, "unit": UNIT,
+                                "h2d_bytes_per_step": s.f_bytes() / k_e2e,
+                                "d2h_bytes_per_step": (s.f_bytes() + 8) / k_e2e,
+                                "steps": k_e2e}
+                del host, hout
+            del f
+            s.close()
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        result[prec_name] = entry
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    r32, r64 = result["fp32"], result["fp64"]
+    nk = W["nk"]
+    flops_launch = theta_flops_per_cell(nk) * cells * len(W["nuclei"])
+    achieved = flops_launch / (r32["theta_ms"] / 1e3) / 1e12
+    peak = fp32_alu_peak_tflops()
+    tr = committed_traffic()
+    line = {
+        "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r32["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (hydrogen 1s Wigner function computed on the GPU)",
+        "config": {"workload": W["name"], "cells": cells, "global_batch": world,
+                   "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (f = %.1f GB)" % (cells * 4 / 1e9)},
+        "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
+                 "dtype": "f64"},
+        "mass_drift_rel": {"fp32": (r32["mass"] - r32["mass0"]) / r32["mass0"],
+                           "fp64": (r64["mass"] - r64["mass0"]) / r64["mass0"]},
+        "roofline": {"kernel": "k_theta (one Horner stage of P: Theta^T over all x points)",
+                     "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "ms_per_launch": r32["theta_ms"],
+                     "traffic": (tr["dram_bytes_per_launch"] * cells / tr["cells"]) if tr else None},
+        "e2e": r32["e2e"],
+        "gpu_launches": 10 * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": base,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_profile(args):
+    """FP32 form only: init, W warm-up steps and K steps, nothing else (for ncu)."""
+    import torch
+    import paper_2205_02380_gb300 as ch
+    W = WORKLOAD
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = make_solver(ch, ch.FP32_MIXED, stream)
+        f = torch.empty((W["nx"],) * 3 + (W["nk"],) * 3, device="cuda", dtype=torch.float32)
+        s.init_hydrogen_1s(f, n_y=W["n_y"])
+        ms = time_steps(torch, s, f, W["dt"], args.steps, args.warmup, stream, None)
+        s.close()
+    print(json.dumps({"profile_ms_per_step": ms / max(1, args.steps), "nx": W["nx"]}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="chasm", choices=["chasm", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="FP32 timed steps only (no FP64, e2e, baseline or clocks): for ncu captures")
+    ap.add_argument("--nx", type=int, default=None, help="override N_x (profiling on smaller cases)")
+    ap.add_argument("--sample-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.nx:
+        WORKLOAD["nx"] = args.nx
+        WORKLOAD["name"] = WORKLOAD["name"].replace("32^3x32^3", f"{args.nx}^3x32^3")
+    if args.profile:
+        run_profile(args)
+        return
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.sample_seconds)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_chasm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -209,39 +209,44 @@ def _feet_taps(n: int, h: float, alpha: np.ndarray):
     return nus.astype(np.int64), w
 
 
-def advect(f: np.ndarray, prob: Problem, tau: float) -> np.ndarray:
+def advect(f: np.ndarray, prob: Problem, tau: float, kaxes=None) -> np.ndarray:
     """A(tau): f(x - hbar k tau / m, k) by the tensor-product cubic spline (Eqs. 2.6, 3.10).
 
     eta from spline_coeffs_3d; then, per output point, the literal 4x4x4 = 64-term sum
     sum_{nu1,nu2,nu3} eta * prod_d B_{nu_d}(x_{j_d} - alpha_d h_d), alpha_d = hbar k_d tau/(m h_d).
-    Coefficients with nu outside [-1, N+1] are zero (ghost splines)."""
+    Coefficients with nu outside [-1, N+1] are zero (ghost splines).
+
+    kaxes: optional (k1 values, k2 values, k3 values) of the last three axes of f, for inputs
+    that hold a subset of the k-grid (each k is independent in A); default the full k-grid."""
     eta = spline_coeffs_3d(f, prob)
-    nk = prob.nk
-    ks = prob.ks()
+    if kaxes is None:
+        kaxes = (prob.ks(),) * 3
+    kn = [len(kaxes[d]) for d in range(3)]
     taps = []
     pad = 0
     for d in range(3):
-        alpha = prob.hbar * ks * tau / (prob.m * prob.hs(d))
+        alpha = prob.hbar * np.asarray(kaxes[d], dtype=np.float64) * tau / (prob.m * prob.hs(d))
         nu, w = _feet_taps(prob.nx[d], prob.hs(d), alpha)
         taps.append((nu, w))
         pad = max(pad, int(np.max(np.abs(nu))) + 2)
     # zero-pad eta so every nu in range maps to a zero ghost; array index of nu is nu + 1 + pad
     eta_p = np.pad(eta, [(pad, pad)] * 3 + [(0, 0)] * 3)
     n1, n2, n3 = prob.nx
-    K1 = np.arange(nk).reshape(1, 1, 1, nk, 1, 1)
-    K2 = np.arange(nk).reshape(1, 1, 1, 1, nk, 1)
-    K3 = np.arange(nk).reshape(1, 1, 1, 1, 1, nk)
-    out = np.zeros(prob.shape)
+    m1, m2, m3 = kn
+    K1 = np.arange(m1).reshape(1, 1, 1, m1, 1, 1)
+    K2 = np.arange(m2).reshape(1, 1, 1, 1, m2, 1)
+    K3 = np.arange(m3).reshape(1, 1, 1, 1, 1, m3)
+    out = np.zeros(tuple(prob.nx) + tuple(kn))
     (nu1, w1), (nu2, w2), (nu3, w3) = taps
     for a in range(4):
-        I1 = (nu1[:, :, a] + 1 + pad).reshape(n1, 1, 1, nk, 1, 1)
-        W1 = w1[:, :, a].reshape(n1, 1, 1, nk, 1, 1)
+        I1 = (nu1[:, :, a] + 1 + pad).reshape(n1, 1, 1, m1, 1, 1)
+        W1 = w1[:, :, a].reshape(n1, 1, 1, m1, 1, 1)
         for b in range(4):
-            I2 = (nu2[:, :, b] + 1 + pad).reshape(1, n2, 1, 1, nk, 1)
-            W2 = w2[:, :, b].reshape(1, n2, 1, 1, nk, 1)
+            I2 = (nu2[:, :, b] + 1 + pad).reshape(1, n2, 1, 1, m2, 1)
+            W2 = w2[:, :, b].reshape(1, n2, 1, 1, m2, 1)
             for c in range(4):
-                I3 = (nu3[:, :, c] + 1 + pad).reshape(1, 1, n3, 1, 1, nk)
-                W3 = w3[:, :, c].reshape(1, 1, n3, 1, 1, nk)
+                I3 = (nu3[:, :, c] + 1 + pad).reshape(1, 1, n3, 1, 1, m3)
+                W3 = w3[:, :, c].reshape(1, 1, n3, 1, 1, m3)
                 out += W1 * W2 * W3 * eta_p[I1, I2, I3, K1, K2, K3]
     return out
 
@@ -373,15 +378,21 @@ def theta_coulomb_point(fk: np.ndarray, xt: np.ndarray, Z: float, hbar: float, k
 
 
 def theta_coulomb(f: np.ndarray, prob: Problem, T: np.ndarray | None = None,
-                  x_batch: int = 64) -> np.ndarray:
-    """Theta^T[f] on the whole grid: sum over nuclei of theta_coulomb_point (Sec. 4)."""
+                  x_batch: int = 64, xpts: np.ndarray | None = None) -> np.ndarray:
+    """Theta^T[f] on the whole grid: sum over nuclei of theta_coulomb_point (Sec. 4).
+
+    xpts: optional (n, 3) positions of the leading axis of f (shape (n, Nk, Nk, Nk)), for
+    inputs that hold a subset of the x points (Theta is local in x); default the full x-grid."""
     if T is None:
         T = tkm_tensor(prob.nk, prob.lk)
     ks = prob.ks()
-    X = np.stack(np.meshgrid(prob.xs(0), prob.xs(1), prob.xs(2), indexing="ij"), axis=-1)
     nk = prob.nk
+    if xpts is None:
+        X = np.stack(np.meshgrid(prob.xs(0), prob.xs(1), prob.xs(2), indexing="ij"), axis=-1)
+        Xf = X.reshape(-1, 3)
+    else:
+        Xf = np.asarray(xpts, dtype=np.float64).reshape(-1, 3)
     fx = f.reshape(-1, nk, nk, nk)
-    Xf = X.reshape(-1, 3)
     out = np.zeros_like(fx)
     for pos, Z in prob.nuclei:
         xt = Xf - np.asarray(pos, dtype=np.float64)
@@ -391,14 +402,15 @@ def theta_coulomb(f: np.ndarray, prob: Problem, T: np.ndarray | None = None,
     return out.reshape(f.shape)
 
 
-def pflow_coulomb(f: np.ndarray, prob: Problem, dt: float, T: np.ndarray | None = None) -> np.ndarray:
+def pflow_coulomb(f: np.ndarray, prob: Problem, dt: float, T: np.ndarray | None = None,
+                  xpts: np.ndarray | None = None) -> np.ndarray:
     """P(dt) for the Coulomb case: the 4-term Taylor approximation of exp(dt Theta^T) in Horner
     form, u <- f + (dt/s) Theta^T[u] for s = 4, 3, 2, 1 starting from u = f."""
     if T is None:
         T = tkm_tensor(prob.nk, prob.lk)
     u = f
     for s in (4, 3, 2, 1):
-        u = f + (dt / s) * theta_coulomb(u, prob, T)
+        u = f + (dt / s) * theta_coulomb(u, prob, T, xpts=xpts)
     return u
 
 

@@ -1,0 +1,119 @@
+// Internal host-side declarations shared by the translation units of libchasm.
+// Not part of the public ABI (include/chasm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/chasm.h"
+
+namespace chasm {
+
+constexpr int kMaxNuclei = 8;
+
+// Device-side description of the grid used by every kernel.
+struct GridDesc {
+  int nx[3];        // x points per dimension
+  int nk;           // k points per dimension
+  int64_t nxp;      // nx0 * nx1 * nx2 (x points)
+  int64_t kvol;     // nk^3 (cells per x point)
+  int64_t ncell;    // nxp * kvol
+  double h[3];      // x spacings
+  double x_lo[3];
+  double lk;        // k half-width
+  double dk;        // 2 lk / nk
+};
+
+// Per-dimension advection tables for one tau (A(tau), Sec. 3.2): for every k index the integer
+// part n = floor(alpha) and the four B-spline weights (b4, b3, b2, b1)(alpha - n) of Eq. 3.7.
+struct AdvectTables {
+  double tau = 0.0;
+  bool valid = false;
+  void* dev = nullptr;      // [3][nk] weights (T x4) followed by [3][nk] int shifts
+};
+
+struct Handle;
+
+// ---- kernel launchers (defined in the .cu files) ----
+// advection (k_advect.cu)
+constexpr int kAdvectThreads = 128;
+constexpr int kAdvectMaxSmem = 200 * 1024;
+cudaError_t advect_prepare();
+cudaError_t launch_advect_dim(const Handle& H, void* f, int dim, cudaStream_t s);
+// Coulomb operator (k_theta.cu): out = (base or 0) + sum_a coef[a] * Theta_a[in]
+cudaError_t launch_theta(const Handle& H, const void* in, const void* base, void* out,
+                         const double* coef, cudaStream_t s);
+int theta_grid_blocks(const Handle& H);
+size_t theta_scratch_bytes(int nk, bool fp64, int blocks);
+int theta_occupancy_blocks(int nk, bool fp64, int device);
+// symbol precompute (k_symbol.cu): T (FP64, (2N-1)^3) and T-hat (parity-major, scaled)
+cudaError_t compute_symbol(int nk, double lk, double* T_dev, void* that_dev, bool fp64,
+                           double* that_absmax_host, cudaStream_t s);
+// misc (k_misc.cu)
+cudaError_t launch_moments(const Handle& H, const void* f, double* partials, double* result_dev,
+                           cudaStream_t s);
+cudaError_t launch_kshift(const Handle& H, void* f, int dim, const void* rows, cudaStream_t s);
+cudaError_t launch_init_gaussians(const Handle& H, void* f, const chasm_gaussian* g, int n,
+                                  cudaStream_t s);
+cudaError_t launch_init_1s(const Handle& H, void* f, int n_y, const double c[3], cudaStream_t s,
+                           std::string* err);
+int moments_blocks();
+
+struct Handle {
+  chasm_grid grid{};
+  chasm_box box{};
+  double hbar = 1.0, m = 1.0;
+  chasm_options opt{};
+  std::vector<chasm_nucleus> nuclei;
+  double kappa = 0.0;
+  double center[3] = {0, 0, 0};
+  bool fp64 = false;
+  size_t elt = 4;
+  GridDesc g{};
+  int device = 0;
+  int num_sms = 0;
+
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+
+  // PMBC end stencils (Eq. 3.5) and LU factors of the Hermite-closed system per dimension
+  int J[3] = {0, 0, 0};            // stencil lengths min(n_nb, N) + 1
+  double* d_cplus[3] = {nullptr, nullptr, nullptr};
+  double* d_cminus[3] = {nullptr, nullptr, nullptr};
+  void* d_lu[3] = {nullptr, nullptr, nullptr};   // [cprime (n) | mult (n)] in storage type
+
+  AdvectTables adv;                // current tau tables
+  // Coulomb
+  double* d_T = nullptr;           // FP64 T_p, (2N-1)^3
+  void* d_that = nullptr;          // T-hat, storage type, (2N)^3 parity-major, / (2N)^3
+  double that_absmax = 0.0;
+  void* d_phase = nullptr;         // modulation tables (storage type complex)
+  int theta_blocks = 0;
+  void* d_scratch = nullptr;       // per-CTA scratch of the Theta kernel
+  void* d_u[2] = {nullptr, nullptr};  // Horner buffers
+  // harmonic
+  void* d_krows = nullptr;         // circulant rows [3][nx_d][nk] for the current dt
+  double krows_dt = 0.0;
+  bool krows_valid = false;
+  // reductions
+  double* d_partials = nullptr;
+  double* d_result = nullptr;
+  double* d_vx = nullptr;          // V(x) per x point (FP64)
+  // host-buffer entry point
+  void* d_fhost = nullptr;
+  // step graph cache
+  cudaGraphExec_t graph = nullptr;
+  void* graph_f = nullptr;
+  double graph_dt = 0.0;
+
+  std::string err;
+  size_t workspace = 0;
+};
+
+// Returns a message for the last error on this thread when no handle exists.
+void set_thread_error(const std::string& e);
+
+}  // namespace chasm

@@ -1,0 +1,345 @@
+// Reductions (mass, energy), the quadratic-potential P-flow and the initial-data kernels.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.hpp"
+
+namespace chasm {
+namespace {
+
+constexpr int kMomBlocks = 1024;   // fixed: the reduction tree does not depend on the device
+constexpr int kMomThreads = 256;
+
+// ---------------------------------------------------------------------------------------------
+// Mass and energy (diagnostics of Sec. 5): per x point, S0 = sum_k f and S2 = sum_k |k|^2 f;
+// mass += S0, energy += (hbar^2/2m) dk^2 S2' + V(x) S0 where S2' uses integer |j - N/2|^2.
+// Each block owns a fixed set of x points and reduces them in a fixed order; a second kernel
+// adds the block partials in a fixed order, so the result is bitwise reproducible.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kMomThreads) k_moments(const T* __restrict__ f, int64_t nxp,
+                                                         int nk, const double* __restrict__ vx,
+                                                         double* __restrict__ partials) {
+  __shared__ double red[2][kMomThreads / 32];
+  const int tid = threadIdx.x;
+  const int kvol = nk * nk * nk;
+  double bm = 0.0, bk = 0.0, bv = 0.0;   // block accumulators (thread 0)
+  for (int64_t xp = blockIdx.x; xp < nxp; xp += gridDim.x) {
+    const T* fx = f + xp * kvol;
+    double s0 = 0.0, s2 = 0.0;
+    for (int e = tid; e < kvol; e += kMomThreads) {
+      const double v = (double)fx[e];
+      const int k3 = e % nk - nk / 2, k2 = (e / nk) % nk - nk / 2, k1 = e / (nk * nk) - nk / 2;
+      s0 += v;
+      s2 += v * (double)(k1 * k1 + k2 * k2 + k3 * k3);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = s0;
+      red[1][tid >> 5] = s2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < kMomThreads / 32; ++w) {
+        a += red[0][w];
+        b += red[1][w];
+      }
+      bm += a;                 // sum f
+      bk += b;                 // sum |j - N/2|^2 f  (kinetic, in units of dk^2)
+      bv += vx[xp] * a;        // sum V(x) f
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    partials[(int64_t)3 * blockIdx.x + 0] = bm;
+    partials[(int64_t)3 * blockIdx.x + 1] = bk;
+    partials[(int64_t)3 * blockIdx.x + 2] = bv;
+  }
+}
+
+__global__ void k_moments_final(const double* __restrict__ partials, int nblocks, double cell,
+                                double kin_fac, double* __restrict__ out) {
+  __shared__ double red[3][kMomThreads];
+  const int tid = threadIdx.x;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = tid; i < nblocks; i += kMomThreads) {
+    a += partials[3 * i];
+    b += partials[3 * i + 1];
+    c += partials[3 * i + 2];
+  }
+  red[0][tid] = a;
+  red[1][tid] = b;
+  red[2][tid] = c;
+  __syncthreads();
+  for (int s = kMomThreads / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+      red[0][tid] += red[0][tid + s];
+      red[1][tid] += red[1][tid + s];
+      red[2][tid] += red[2][tid + s];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    out[0] = red[0][0] * cell;
+    out[1] = (red[1][0] * kin_fac + red[2][0]) * cell;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Quadratic potential: P(dt) is the exact shift f(x, k + s(x)), s_d = dt kappa (x_d - c_d)/hbar
+// (Eq. 5.1).  Per k-dimension it is the band-limited (periodic, spectral) shift, i.e. a circulant
+// matrix whose first column c[q] = (1/N) sum_m phi_m e^{2 pi i m q / N} is tabulated per x_d on
+// the host; one thread applies it to one k-line in registers.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void k_kshift(T* __restrict__ f, int64_t nxp, int nx1, int nx2, int nx3, int dim,
+                         const T* __restrict__ rows) {
+  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= nxp * N * N) return;
+  const int64_t xp = line / (N * N);
+  const int r = (int)(line % (N * N));
+  int64_t base, stride;
+  int id;
+  if (dim == 0) {
+    base = xp * N * N * N + r;
+    stride = N * N;
+    id = (int)(xp / ((int64_t)nx2 * nx3));
+  } else if (dim == 1) {
+    base = xp * N * N * N + (r / N) * N * N + (r % N);
+    stride = N;
+    id = nx1 + (int)((xp / nx3) % nx2);
+  } else {
+    base = xp * N * N * N + (int64_t)r * N;
+    stride = 1;
+    id = nx1 + nx2 + (int)(xp % nx3);
+  }
+  const T* crow = rows + (int64_t)id * N;
+  T c[N], v[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) c[q] = __ldg(crow + q);
+#pragma unroll
+  for (int l = 0; l < N; ++l) v[l] = f[base + l * stride];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    T acc = (T)0;
+#pragma unroll
+    for (int l = 0; l < N; ++l) acc += c[(j - l + N) & (N - 1)] * v[l];
+    f[base + j * stride] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Initial data
+// ---------------------------------------------------------------------------------------------
+struct Packets {
+  int n;
+  chasm_gaussian g[16];
+};
+
+template <typename T>
+__global__ void k_init_gauss(T* __restrict__ f, GridDesc gd, Packets P) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= gd.ncell) return;
+  const int nk = gd.nk;
+  const int64_t xp = i / gd.kvol;
+  const int e = (int)(i % gd.kvol);
+  const int i3 = (int)(xp % gd.nx[2]), i2 = (int)((xp / gd.nx[2]) % gd.nx[1]);
+  const int i1 = (int)(xp / ((int64_t)gd.nx[2] * gd.nx[1]));
+  const double x[3] = {gd.x_lo[0] + i1 * gd.h[0], gd.x_lo[1] + i2 * gd.h[1], gd.x_lo[2] + i3 * gd.h[2]};
+  const double k[3] = {(e / (nk * nk) - nk / 2) * gd.dk, ((e / nk) % nk - nk / 2) * gd.dk,
+                       (e % nk - nk / 2) * gd.dk};
+  double s = 0.0;
+  for (int p = 0; p < P.n; ++p) {
+    const chasm_gaussian& g = P.g[p];
+    double rx = 0.0, rk = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      rx += (x[d] - g.x0[d]) * (x[d] - g.x0[d]);
+      rk += (k[d] - g.k0[d]) * (k[d] - g.k0[d]);
+    }
+    s += g.w * exp(-g.ax * rx - g.ak * rk);
+  }
+  f[i] = (T)s;
+}
+
+// Hydrogen 1s Wigner function, discrete Fourier sum of Sec. 5.2.  Because dk dy = 2 pi / N the
+// phase is N-periodic in the sample index, so the N_y^3 samples fold into N^3 bins (this
+// kernel), followed by an N^3 DFT (three separable passes) and the dy^3 factor.
+struct OneS {
+  double x_lo[3], h[3];
+  double c[3];
+  double dy;
+  int nx[3];
+  int nk, ny;
+  int64_t xp0, nxl;   // first x point of the chunk and its length
+};
+
+__global__ void k_1s_fold(double2* __restrict__ P, OneS o) {
+  const int N = o.nk;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= o.nxl * N * N * N) return;
+  const int64_t xp = o.xp0 + t / (N * N * N);
+  const int r = (int)(t % (N * N * N));
+  const int r3 = r % N, r2 = (r / N) % N, r1 = r / (N * N);
+  const int i3 = (int)(xp % o.nx[2]), i2 = (int)((xp / o.nx[2]) % o.nx[1]);
+  const int i1 = (int)(xp / ((int64_t)o.nx[2] * o.nx[1]));
+  const double a1 = o.x_lo[0] + i1 * o.h[0] - o.c[0];
+  const double a2 = o.x_lo[1] + i2 * o.h[1] - o.c[1];
+  const double a3 = o.x_lo[2] + i3 * o.h[2] - o.c[2];
+  const int rep = o.ny / N;
+  const double norm = 1.0 / (8.0 * 3.141592653589793 * 3.141592653589793 * 3.141592653589793 *
+                             3.141592653589793);   // (2 sqrt 2 pi^2)^-2
+  double s = 0.0;
+  for (int b1 = 0; b1 < rep; ++b1) {
+    const double y1 = (double)(r1 + b1 * N - o.ny / 2) * o.dy * 0.5;
+    const double m1 = (a1 - y1) * (a1 - y1), p1 = (a1 + y1) * (a1 + y1);
+    for (int b2 = 0; b2 < rep; ++b2) {
+      const double y2 = (double)(r2 + b2 * N - o.ny / 2) * o.dy * 0.5;
+      const double m2 = m1 + (a2 - y2) * (a2 - y2), p2 = p1 + (a2 + y2) * (a2 + y2);
+      for (int b3 = 0; b3 < rep; ++b3) {
+        const double y3 = (double)(r3 + b3 * N - o.ny / 2) * o.dy * 0.5;
+        const double rm = sqrt(m2 + (a3 - y3) * (a3 - y3));
+        const double rp = sqrt(p2 + (a3 + y3) * (a3 + y3));
+        s += exp(-(rm + rp));
+      }
+    }
+  }
+  P[t] = make_double2(s * norm, 0.0);
+}
+
+// out[.., j, ..] = sum_r in[.., r, ..] e^{-2 pi i (j - N/2) r / N} along one k axis
+__global__ void k_1s_dft(const double2* __restrict__ in, double2* __restrict__ out, int64_t nxl,
+                         int N, int axis) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nxl * N * N * N) return;
+  const int64_t cell0 = t - t % ((int64_t)N * N * N);
+  const int e = (int)(t % (N * N * N));
+  const int stride = axis == 0 ? N * N : (axis == 1 ? N : 1);
+  const int j = (e / stride) % N;
+  const int64_t lb = cell0 + (e - j * stride);
+  double re = 0.0, im = 0.0;
+  for (int r = 0; r < N; ++r) {
+    long long q = (long long)(j - N / 2) * r;
+    q %= N;
+    if (q < 0) q += N;
+    double sn, cs;
+    sincospi(-2.0 * (double)q / N, &sn, &cs);
+    const double2 v = in[lb + (int64_t)r * stride];
+    re += v.x * cs - v.y * sn;
+    im += v.x * sn + v.y * cs;
+  }
+  out[t] = make_double2(re, im);
+}
+
+template <typename T>
+__global__ void k_1s_store(const double2* __restrict__ P, T* __restrict__ f, int64_t off,
+                           int64_t n, double scale) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  f[off + t] = (T)(P[t].x * scale);
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+int moments_blocks() { return kMomBlocks; }
+
+cudaError_t launch_moments(const Handle& H, const void* f, double* partials, double* result_dev,
+                           cudaStream_t s) {
+  const int nb = (int)std::min<int64_t>(kMomBlocks, H.g.nxp);
+  if (H.fp64)
+    k_moments<double><<<nb, kMomThreads, 0, s>>>((const double*)f, H.g.nxp, H.g.nk, H.d_vx, partials);
+  else
+    k_moments<float><<<nb, kMomThreads, 0, s>>>((const float*)f, H.g.nxp, H.g.nk, H.d_vx, partials);
+  const double cell = H.g.h[0] * H.g.h[1] * H.g.h[2] * H.g.dk * H.g.dk * H.g.dk;
+  const double kin = H.hbar * H.hbar / (2.0 * H.m) * H.g.dk * H.g.dk;
+  k_moments_final<<<1, kMomThreads, 0, s>>>(partials, nb, cell, kin, result_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kshift(const Handle& H, void* f, int dim, const void* rows, cudaStream_t s) {
+  const int64_t lines = H.g.nxp * H.g.nk * H.g.nk;
+  const unsigned nb = nblk(lines, 128);
+  const int* nx = H.g.nx;
+#define CHASM_KS(TT, NN) \
+  k_kshift<TT, NN><<<nb, 128, 0, s>>>((TT*)f, H.g.nxp, nx[0], nx[1], nx[2], dim, (const TT*)rows)
+  switch (H.g.nk) {
+    case 8:
+      if (H.fp64) CHASM_KS(double, 8); else CHASM_KS(float, 8);
+      break;
+    case 16:
+      if (H.fp64) CHASM_KS(double, 16); else CHASM_KS(float, 16);
+      break;
+    case 32:
+      if (H.fp64) CHASM_KS(double, 32); else CHASM_KS(float, 32);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef CHASM_KS
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_gaussians(const Handle& H, void* f, const chasm_gaussian* g, int n,
+                                  cudaStream_t s) {
+  Packets P;
+  P.n = n;
+  for (int i = 0; i < n; ++i) P.g[i] = g[i];
+  const unsigned nb = nblk(H.g.ncell, 256);
+  if (H.fp64)
+    k_init_gauss<double><<<nb, 256, 0, s>>>((double*)f, H.g, P);
+  else
+    k_init_gauss<float><<<nb, 256, 0, s>>>((float*)f, H.g, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_1s(const Handle& H, void* f, int n_y, const double c[3], cudaStream_t s,
+                           std::string* err) {
+  const int N = H.g.nk;
+  const int64_t kvol = H.g.kvol;
+  const size_t per_x = (size_t)kvol * sizeof(double2) * 2;
+  int64_t chunk = std::max<int64_t>(1, (int64_t)((size_t)2 << 30) / (int64_t)per_x);
+  chunk = std::min<int64_t>(chunk, H.g.nxp);
+  double2 *A = nullptr, *B = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&A, (size_t)chunk * kvol * sizeof(double2), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&B, (size_t)chunk * kvol * sizeof(double2), s);
+  if (e != cudaSuccess) {
+    if (err) *err = "init_hydrogen_1s: temporary allocation failed";
+    if (A) cudaFreeAsync(A, s);
+    return e;
+  }
+  OneS o;
+  for (int d = 0; d < 3; ++d) {
+    o.x_lo[d] = H.g.x_lo[d];
+    o.h[d] = H.g.h[d];
+    o.c[d] = c ? c[d] : 0.0;
+    o.nx[d] = H.g.nx[d];
+  }
+  o.nk = N;
+  o.ny = n_y;
+  o.dy = 2.0 * M_PI / (N * H.g.dk);
+  const double scale = o.dy * o.dy * o.dy;
+  for (int64_t x0 = 0; x0 < H.g.nxp && e == cudaSuccess; x0 += chunk) {
+    o.xp0 = x0;
+    o.nxl = std::min<int64_t>(chunk, H.g.nxp - x0);
+    const int64_t n = o.nxl * kvol;
+    k_1s_fold<<<nblk(n, 128), 128, 0, s>>>(A, o);
+    k_1s_dft<<<nblk(n, 256), 256, 0, s>>>(A, B, o.nxl, N, 2);
+    k_1s_dft<<<nblk(n, 256), 256, 0, s>>>(B, A, o.nxl, N, 1);
+    k_1s_dft<<<nblk(n, 256), 256, 0, s>>>(A, B, o.nxl, N, 0);
+    if (H.fp64)
+      k_1s_store<double><<<nblk(n, 256), 256, 0, s>>>(B, (double*)f, x0 * kvol, n, scale);
+    else
+      k_1s_store<float><<<nblk(n, 256), 256, 0, s>>>(B, (float*)f, x0 * kvol, n, scale);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(A, s);
+  cudaFreeAsync(B, s);
+  return e;
+}
+
+}  // namespace chasm

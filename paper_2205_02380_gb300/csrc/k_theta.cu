@@ -1,0 +1,494 @@
+// Coulomb pseudodifferential operator by the truncated kernel method (Sec. 4).
+//
+//   Theta^T[u](x, k_p) = sum_A coef_A Im[ e^{2i(x-x_A).k_p} Phi_p ],
+//   Phi_p = sum_q T_{p-q} u_q e^{-2i(x-x_A).k_q}                      (Eqs. 4.1, 4.5, 4.6)
+//   coef_A = -(2 Z_A / (pi^2 hbar)) * c   (the Eq. 2.3 sign; c = Horner factor or 1)
+//
+// The linear convolution with T ((2N-1)^3 taps) is a circular convolution of length 2N per
+// dimension (twofold zero padding, Sec. 4.1), diagonalised by the DFT: Phi = IDFT(T-hat DFT(g)).
+// Each padded length-2N transform is split by frequency parity xi = 2j + r into two length-N
+// transforms of the input twisted by tw_r[n] = e^{-i pi r n / N} (forward) and the same split
+// on the inverse side with the conjugate twist, keeping only the N unpadded outputs.  All
+// transforms are therefore length-N FFTs held entirely in registers (one line per thread,
+// fully unrolled radix-2, no shared-memory traffic inside a transform).
+//
+// One CTA processes one x point at a time (persistent loop over x points), per nucleus:
+//   Phase A  2N^2 jobs (k1, k2, r3): load the u line along k3, modulate, twist, FFT_N
+//            -> G[s3][k1][k2] in the CTA's global scratch (s3 = r3 N + j3, parity-major).
+//   Phase B  for each of the 2N slabs s3 (NG slabs in parallel, one group of 4N threads each):
+//            B1 FFT along k2 (2N jobs), B2 along k1: FFT, multiply by T-hat, inverse FFT (4N
+//            jobs), B3 inverse along k2 (2N jobs) and parity combine; in shared memory.
+//   Phase C  2N^2 jobs: inverse FFT along k3, demodulate, Im, scale, accumulate per parity.
+//   Phase D  out = base + acc_0 + acc_1 (coalesced).
+// T-hat is stored in parity-major order [s3][s1][s2] with the 1/(2N)^3 normalisation folded in.
+#include "internal.hpp"
+
+namespace chasm {
+namespace {
+
+template <typename T>
+struct cpx {
+  T re, im;
+};
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> conjg(cpx<T> a) {
+  return {a.re, -a.im};
+}
+
+// ---- twiddle tables: cos(2 pi k / 64), sin(2 pi k / 64), k = 0..63, evaluated at compile time
+// by Taylor series after exact octant reduction (own implementation, no libm). ----
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double ce_sin_series(double x) {
+  double t = x, s = x;
+  for (int i = 1; i < 16; ++i) {
+    t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+    s += t;
+  }
+  return s;
+}
+constexpr double ce_cos_series(double x) {
+  double t = 1.0, s = 1.0;
+  for (int i = 1; i < 16; ++i) {
+    t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+    s += t;
+  }
+  return s;
+}
+// cos(2 pi k / n) for n divisible by 8
+constexpr double ce_cos2pi(int k, int n) {
+  k %= n;
+  if (k < 0) k += n;
+  if (2 * k > n) k = n - k;          // cos is even: k in [0, n/2]
+  double sg = 1.0;
+  if (4 * k > n) {                    // cos(pi - a) = -cos(a)
+    k = n / 2 - k;
+    sg = -1.0;
+  }
+  // k in [0, n/4]
+  return (8 * k > n) ? sg * ce_sin_series(2.0 * kPi * (n / 4 - k) / n)
+                     : sg * ce_cos_series(2.0 * kPi * k / n);
+}
+constexpr double ce_sin2pi(int k, int n) { return ce_cos2pi(k - n / 4, n); }
+
+#define CHASM_C4(f, b) f(b, 64), f(b + 1, 64), f(b + 2, 64), f(b + 3, 64)
+#define CHASM_C16(f, b) CHASM_C4(f, b), CHASM_C4(f, b + 4), CHASM_C4(f, b + 8), CHASM_C4(f, b + 12)
+#define CHASM_C64(f) CHASM_C16(f, 0), CHASM_C16(f, 16), CHASM_C16(f, 32), CHASM_C16(f, 48)
+__constant__ double c_cos64d[64] = {CHASM_C64(ce_cos2pi)};
+__constant__ double c_sin64d[64] = {CHASM_C64(ce_sin2pi)};
+__constant__ float c_cos64f[64] = {CHASM_C64((float)ce_cos2pi)};
+__constant__ float c_sin64f[64] = {CHASM_C64((float)ce_sin2pi)};
+
+template <typename T>
+__device__ __forceinline__ T tw_cos(int k);
+template <typename T>
+__device__ __forceinline__ T tw_sin(int k);
+template <>
+__device__ __forceinline__ float tw_cos<float>(int k) { return c_cos64f[k]; }
+template <>
+__device__ __forceinline__ float tw_sin<float>(int k) { return c_sin64f[k]; }
+template <>
+__device__ __forceinline__ double tw_cos<double>(int k) { return c_cos64d[k]; }
+template <>
+__device__ __forceinline__ double tw_sin<double>(int k) { return c_sin64d[k]; }
+
+template <int N>
+__host__ __device__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1; b < N; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// In-register radix-2 DIT FFT of length N (N | 32).  Forward: X_j = sum_n x_n e^{-2 pi i jn/N};
+// inverse (INV): unnormalised, e^{+2 pi i jn/N}.  Natural order in and out.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void fft(T (&re)[N], T (&im)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int j = bitrev<N>(i);
+    if (j > i) {
+      T t = re[i];
+      re[i] = re[j];
+      re[j] = t;
+      t = im[i];
+      im[i] = im[j];
+      im[j] = t;
+    }
+  }
+#pragma unroll
+  for (int half = 1; half < N; half <<= 1) {
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const int k64 = j * (32 / half);  // twiddle e^{-+2 pi i j / (2 half)} = entry k64 of 64
+#pragma unroll
+      for (int i = j; i < N; i += 2 * half) {
+        const T xr = re[i + half], xi = im[i + half];
+        T tr, ti;
+        if (k64 == 0) {
+          tr = xr;
+          ti = xi;
+        } else if (k64 == 16) {
+          if (!INV) {
+            tr = xi;
+            ti = -xr;
+          } else {
+            tr = -xi;
+            ti = xr;
+          }
+        } else {
+          const T c = tw_cos<T>(k64), s = tw_sin<T>(k64);
+          if (!INV) {
+            tr = xr * c + xi * s;
+            ti = xi * c - xr * s;
+          } else {
+            tr = xr * c - xi * s;
+            ti = xi * c + xr * s;
+          }
+        }
+        re[i + half] = re[i] - tr;
+        im[i + half] = im[i] - ti;
+        re[i] += tr;
+        im[i] += ti;
+      }
+    }
+  }
+}
+
+// Twist by tw_1[n] = e^{-i pi n / N} = entry n*32/N of the 64-table (CONJ: e^{+i pi n/N}).
+template <typename T, int N, bool CONJ>
+__device__ __forceinline__ void twist(T (&re)[N], T (&im)[N]) {
+#pragma unroll
+  for (int n = 1; n < N; ++n) {
+    const int k64 = n * (32 / N);
+    const T c = tw_cos<T>(k64), s = CONJ ? tw_sin<T>(k64) : -tw_sin<T>(k64);
+    const T a = re[n], b = im[n];
+    re[n] = a * c - b * s;
+    im[n] = a * s + b * c;
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void load_line(const T* __restrict__ src, T (&v)[N]) {
+  if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+      const float4 t = s4[q];
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
+    }
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) {
+      const double2 t = s2[q];
+      v[2 * q] = (T)t.x;
+      v[2 * q + 1] = (T)t.y;
+    }
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void store_line(T* __restrict__ dst, const T (&v)[N]) {
+  if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+    double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) d2[q] = make_double2(v[2 * q], v[2 * q + 1]);
+  }
+}
+
+template <typename T>
+struct ThetaParams {
+  const T* in;
+  const T* base;        // may be null: out = Theta[in]
+  T* out;
+  int64_t nxp;
+  int nx1, nx2, nx3;
+  const T* that;        // [2N][2N][2N] parity-major [s3][s1][s2], scaled by 1/(2N)^3
+  const cpx<T>* ph;     // per nucleus: E1[nx1][N], E2[nx2][N], E3[nx3][4][N] (M0, M1, D0, D1)
+  int64_t ph_stride;
+  int n_nuc;
+  T coef[kMaxNuclei];
+  cpx<T>* G;            // per CTA: 2N^3 complex
+  T* acc;               // per CTA: 2N^3 real
+};
+
+template <int N>
+struct ThetaCfg {
+  static constexpr int NT = 256;
+  static constexpr int L = 2 * N;
+  static constexpr int GS = 4 * N;         // threads per slab group
+  static constexpr int NG = NT / GS;       // slab groups per CTA
+  static constexpr int RS = L + 1;         // padded row stride of the slab buffers
+  static_assert(NT % GS == 0 && L % NG == 0, "slab groups must tile the CTA and the slabs");
+  static constexpr int smem_cpx = NG * 2 * N * RS;
+};
+
+template <typename T, int N, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_theta(const ThetaParams<T> p) {
+  using C = ThetaCfg<N>;
+  constexpr int L = C::L, GS = C::GS, NG = C::NG, RS = C::RS, NT = C::NT;
+  constexpr int N2 = N * N, N3 = N * N * N;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cpx<T>* smem = reinterpret_cast<cpx<T>*>(sm_raw);
+  const int tid = threadIdx.x;
+  const int grp = tid / GS, tg = tid % GS;
+  cpx<T>* V = smem + grp * (2 * N * RS);
+  cpx<T>* Z = V + N * RS;
+  cpx<T>* G = p.G + (size_t)blockIdx.x * (2 * N3);
+  T* acc = p.acc + (size_t)blockIdx.x * (2 * N3);
+
+  for (int64_t xp = blockIdx.x; xp < p.nxp; xp += gridDim.x) {
+    const int i3 = (int)(xp % p.nx3);
+    const int i2 = (int)((xp / p.nx3) % p.nx2);
+    const int i1 = (int)(xp / ((int64_t)p.nx3 * p.nx2));
+    const T* __restrict__ u = p.in + xp * N3;
+
+    for (int a = 0; a < p.n_nuc; ++a) {
+      const cpx<T>* E1 = p.ph + a * p.ph_stride + (int64_t)i1 * N;
+      const cpx<T>* E2 = p.ph + a * p.ph_stride + (int64_t)(p.nx1 + i2) * N;
+      const cpx<T>* E3 = p.ph + a * p.ph_stride + (int64_t)(p.nx1 + p.nx2) * N + (int64_t)i3 * 4 * N;
+      T coef = p.coef[0];   // static indexing keeps the parameter block out of local memory
+#pragma unroll
+      for (int q = 1; q < kMaxNuclei; ++q)
+        if (q == a) coef = p.coef[q];
+
+      // ---- Phase A: modulate + twist + FFT along k3 -> G[s3][k1][k2] ----
+      for (int job = tid; job < 2 * N2; job += NT) {
+        const int r3 = job / N2, line = job % N2;
+        const int k1 = line / N, k2 = line % N;
+        const cpx<T> e12 = conjg(cmul(E1[k1], E2[k2]));
+        T xv[N];
+        load_line<T, N>(u + (size_t)line * N, xv);
+        T re[N], im[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+          const cpx<T> mm = cmul(e12, E3[r3 * N + n]);
+          re[n] = xv[n] * mm.re;
+          im[n] = xv[n] * mm.im;
+        }
+        fft<T, N, false>(re, im);
+        cpx<T>* g = G + (size_t)(r3 * N) * N2 + line;
+#pragma unroll
+        for (int j = 0; j < N; ++j) g[(size_t)j * N2] = {re[j], im[j]};
+      }
+      __syncthreads();
+
+      // ---- Phase B: per slab s3, the 2-D padded convolution in (k1, k2) ----
+      for (int s = grp; s < L; s += NG) {
+        cpx<T>* Gs = G + (size_t)s * N2;
+        for (int e = tg; e < N2; e += GS) Z[(e / N) * (N + 1) + (e % N)] = Gs[e];
+        __syncthreads();
+        if (tg < 2 * N) {  // B1: forward along k2, jobs (r2, k1)
+          const int r2 = tg / N, k1 = tg % N;
+          T re[N], im[N];
+#pragma unroll
+          for (int n = 0; n < N; ++n) {
+            const cpx<T> v = Z[k1 * (N + 1) + n];
+            re[n] = v.re;
+            im[n] = v.im;
+          }
+          if (r2) twist<T, N, false>(re, im);
+          fft<T, N, false>(re, im);
+#pragma unroll
+          for (int j = 0; j < N; ++j) V[k1 * RS + r2 * N + j] = {re[j], im[j]};
+        }
+        __syncthreads();
+        {  // B2: along k1 for column c = (r2, j2): forward, x T-hat, inverse; jobs (r1, c)
+          const int r1 = tg / L, c = tg % L;
+          T re[N], im[N];
+#pragma unroll
+          for (int n = 0; n < N; ++n) {
+            const cpx<T> v = V[n * RS + c];
+            re[n] = v.re;
+            im[n] = v.im;
+          }
+          if (r1) twist<T, N, false>(re, im);
+          fft<T, N, false>(re, im);
+          const T* th = p.that + ((size_t)s * L + r1 * N) * L + c;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const T t = __ldg(th + (size_t)j * L);
+            re[j] *= t;
+            im[j] *= t;
+          }
+          fft<T, N, true>(re, im);
+          if (r1) twist<T, N, true>(re, im);
+          __syncthreads();  // every column of V has been read
+          cpx<T>* dst = r1 ? Z : V;
+#pragma unroll
+          for (int n = 0; n < N; ++n) dst[n * RS + c] = {re[n], im[n]};
+        }
+        __syncthreads();
+        {  // B3: inverse along k2 on V + Z, jobs (r2, n1); parity halves combined through Q
+          T re[N], im[N];
+          const int r2 = tg / N, n1 = tg % N;
+          if (tg < 2 * N) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+              const cpx<T> v = V[n1 * RS + r2 * N + j], w = Z[n1 * RS + r2 * N + j];
+              re[j] = v.re + w.re;
+              im[j] = v.im + w.im;
+            }
+            fft<T, N, true>(re, im);
+            if (r2) twist<T, N, true>(re, im);
+          }
+          __syncthreads();
+          cpx<T>* Q = V;  // Q[r2][n1][n2], row stride N + 1 (aliases V and Z)
+          if (tg < 2 * N) {
+#pragma unroll
+            for (int n = 0; n < N; ++n) Q[(r2 * N + n1) * (N + 1) + n] = {re[n], im[n]};
+          }
+          __syncthreads();
+          for (int e = tg; e < N2; e += GS) {
+            const int n1e = e / N, n2e = e % N;
+            const cpx<T> q0 = Q[n1e * (N + 1) + n2e], q1 = Q[(N + n1e) * (N + 1) + n2e];
+            Gs[e] = {q0.re + q1.re, q0.im + q1.im};
+          }
+          __syncthreads();
+        }
+      }
+
+      // ---- Phase C: inverse along k3, demodulate, Im, scale, accumulate ----
+      for (int job = tid; job < 2 * N2; job += NT) {
+        const int r3 = job / N2, line = job % N2;
+        const int k1 = line / N, k2 = line % N;
+        T re[N], im[N];
+        const cpx<T>* g = G + (size_t)(r3 * N) * N2 + line;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const cpx<T> v = g[(size_t)j * N2];
+          re[j] = v.re;
+          im[j] = v.im;
+        }
+        fft<T, N, true>(re, im);
+        const cpx<T> e12 = cmul(E1[k1], E2[k2]);
+        T val[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+          const cpx<T> z = cmul(e12, E3[(2 + r3) * N + n]);
+          val[n] = coef * (z.re * im[n] + z.im * re[n]);
+        }
+        T* al = acc + (size_t)r3 * N3 + (size_t)line * N;
+        if (a > 0) {
+          T old[N];
+          load_line<T, N>(al, old);
+#pragma unroll
+          for (int n = 0; n < N; ++n) val[n] += old[n];
+        }
+        store_line<T, N>(al, val);
+      }
+      __syncthreads();
+    }
+
+    // ---- Phase D: out = base + acc_0 + acc_1 ----
+    T* __restrict__ o = p.out + xp * N3;
+    const T* __restrict__ b = p.base ? p.base + xp * N3 : nullptr;
+    for (int e = tid; e < N3; e += NT) {
+      const T v = acc[e] + acc[N3 + e];
+      o[e] = b ? b[e] + v : v;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int N>
+constexpr int minb() {
+  return sizeof(T) == 4 ? 2 : 1;
+}
+
+template <typename T, int N>
+size_t smem_bytes() {
+  return (size_t)ThetaCfg<N>::smem_cpx * sizeof(cpx<T>);
+}
+
+template <typename T, int N>
+cudaError_t set_attr() {
+  return cudaFuncSetAttribute(k_theta<T, N, minb<T, N>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes<T, N>());
+}
+
+template <typename T, int N>
+int occupancy(int device) {
+  (void)device;
+  if (set_attr<T, N>() != cudaSuccess) return 1;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_theta<T, N, minb<T, N>()>, 256,
+                                                    smem_bytes<T, N>()) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+template <typename T, int N>
+cudaError_t launch_tn(const Handle& H, const void* in, const void* base, void* out,
+                      const double* coef, cudaStream_t s) {
+  ThetaParams<T> p;
+  p.in = static_cast<const T*>(in);
+  p.base = static_cast<const T*>(base);
+  p.out = static_cast<T*>(out);
+  p.nxp = H.g.nxp;
+  p.nx1 = H.g.nx[0];
+  p.nx2 = H.g.nx[1];
+  p.nx3 = H.g.nx[2];
+  p.that = static_cast<const T*>(H.d_that);
+  p.ph = static_cast<const cpx<T>*>(H.d_phase);
+  p.ph_stride = (int64_t)(H.g.nx[0] + H.g.nx[1] + 4 * H.g.nx[2]) * N;
+  p.n_nuc = (int)H.nuclei.size();
+  for (int a = 0; a < kMaxNuclei; ++a) p.coef[a] = a < p.n_nuc ? (T)coef[a] : (T)0;
+  const int blocks = H.theta_blocks;
+  const size_t per = (size_t)2 * N * N * N;
+  p.G = static_cast<cpx<T>*>(H.d_scratch);
+  p.acc = reinterpret_cast<T*>(static_cast<cpx<T>*>(H.d_scratch) + per * blocks);
+  k_theta<T, N, minb<T, N>()><<<blocks, 256, smem_bytes<T, N>(), s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_theta(const Handle& H, const void* in, const void* base, void* out,
+                         const double* coef, cudaStream_t s) {
+  switch (H.g.nk) {
+    case 8:
+      return H.fp64 ? launch_tn<double, 8>(H, in, base, out, coef, s)
+                    : launch_tn<float, 8>(H, in, base, out, coef, s);
+    case 16:
+      return H.fp64 ? launch_tn<double, 16>(H, in, base, out, coef, s)
+                    : launch_tn<float, 16>(H, in, base, out, coef, s);
+    case 32:
+      return H.fp64 ? launch_tn<double, 32>(H, in, base, out, coef, s)
+                    : launch_tn<float, 32>(H, in, base, out, coef, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int theta_occupancy_blocks(int nk, bool fp64, int device) {
+  switch (nk) {
+    case 8:
+      return fp64 ? occupancy<double, 8>(device) : occupancy<float, 8>(device);
+    case 16:
+      return fp64 ? occupancy<double, 16>(device) : occupancy<float, 16>(device);
+    case 32:
+      return fp64 ? occupancy<double, 32>(device) : occupancy<float, 32>(device);
+  }
+  return 1;
+}
+
+size_t theta_scratch_bytes(int nk, bool fp64, int blocks) {
+  const size_t e = fp64 ? 8 : 4;
+  const size_t per = (size_t)2 * nk * nk * nk;
+  return (size_t)blocks * per * (2 * e + e);
+}
+
+}  // namespace chasm
