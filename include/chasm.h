@@ -157,6 +157,25 @@ int chasm_mass(chasm_handle* h, const void* f_dev, double* out);
 int chasm_energy(chasm_handle* h, const void* f_dev, double* out);
 int chasm_moments(chasm_handle* h, const void* f_dev, double* mass, double* energy);
 
+/* Mass and energy exactly as chasm_moments defines them, for callers that cannot allocate
+ * device memory when they need them: code running while a stream is captured in the global
+ * capture mode (cudaMalloc is not allowed then), services that reserve their whole memory budget
+ * for solves up front, plug-ins that only receive a device pointer.  The paper has no
+ * counterpart; this is a library convenience.  It needs no handle and allocates nothing: its
+ * scratch is a fixed device array of 3 * 262144 + 2 doubles (6 MiB) that the library reserves on
+ * every GPU that loads it until the process exits.  Hence at most 262144 x points
+ * (nx1 nx2 nx3, e.g. 64^3); larger grids are rejected with EINVAL and a message.  f_dev has the
+ * layout and element type (precision) of chasm_step; grid, box and potential are validated as
+ * in chasm_create; mass/energy are host pointers (either may be NULL, not both).  Work runs on
+ * cuda_stream (NULL = legacy default stream) and the call waits for it.  The first call on each
+ * device looks up the array's device address with that device current; make that first call
+ * before any stream capture begins.  All calls share the one array and it keeps the last call's
+ * contents (every entry a call reads is written by that call first), so calls whose work
+ * overlaps on the GPU race with each other: serialise them. */
+int chasm_moments_noalloc(const void* f_dev, const chasm_grid* grid, const chasm_box* box,
+                          const chasm_potential* pot, double hbar, double m, int32_t precision,
+                          void* cuda_stream, double* mass, double* energy);
+
 /* Initial data written on the GPU (asynchronous):
  *   chasm_init_gaussians: f = sum_i w_i exp(-ax_i |x - x0_i|^2 - ak_i |k - k0_i|^2), n >= 1;
  *   chasm_init_hydrogen_1s: the 1s Wigner function of phi = exp(-|x - c|)/(2 sqrt(2) pi^2) by

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchasm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "k_advect.cu", "k_theta.cu", "k_symbol.cu", "k_misc.cu", "server.cu"]
+SOURCES = ["capi.cu", "k_advect.cu", "k_theta.cu", "k_symbol.cu", "k_misc.cu", "server.cu",
+           "noalloc.cu"]
 
 
 def nvcc() -> str:

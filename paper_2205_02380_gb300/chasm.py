@@ -85,6 +85,9 @@ _SIGS = [
     ("chasm_mass", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("chasm_energy", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("chasm_moments", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("chasm_moments_noalloc", C.c_int, [C.c_void_p, C.POINTER(Grid), C.POINTER(Box), C.POINTER(Potential),
+                                        C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("chasm_init_gaussians", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Gaussian), C.c_int32]),
     ("chasm_init_hydrogen_1s", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double)]),
     ("chasm_tkm_tensor", C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
