@@ -1,5 +1,6 @@
 // C ABI of libchasm: argument validation, the plan (PMBC stencils, LU factors, tables, symbol),
 // the Strang step driver with CUDA-graph replay, diagnostics and initial data.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -173,9 +174,27 @@ int build_spline_plan(Handle* H) {
       cm[j] = (-rows[2][N - j + 1] + rows[3][N - j + 1]) / (2.0 * h);
     }
     H->J[d] = J;
-    int rc = upload(H, (void**)&H->d_cplus[d], cp.data(), J * sizeof(double));
-    if (rc) return rc;
-    rc = upload(H, (void**)&H->d_cminus[d], cm.data(), J * sizeof(double));
+    int rc;
+    if (H->fp64) {
+      std::vector<double> c(2 * (size_t)n, 0.0);
+      for (int j = 0; j < J; ++j) {
+        c[j] = cp[j];
+        c[n + j] = cm[j];
+      }
+      rc = upload(H, &H->d_clos[d], c.data(), c.size() * sizeof(double));
+    } else {
+      // unevaluated float pairs hi + lo of the FP64 coefficients
+      std::vector<float> c(4 * (size_t)n, 0.0f);
+      for (int j = 0; j < J; ++j) {
+        c[j] = (float)cp[j];
+        c[n + j] = (float)(cp[j] - (double)c[j]);
+        c[2 * n + j] = (float)cm[j];
+        c[3 * n + j] = (float)(cm[j] - (double)c[2 * n + j]);
+      }
+      rc = upload(H, &H->d_clos[d], c.data(), c.size() * sizeof(float));
+      if (rc) return rc;
+      CHASM_CUDA(H, cudaStreamSynchronize(H->stream));
+    }
     if (rc) return rc;
     CHASM_CUDA(H, cudaStreamSynchronize(H->stream));
     // Thomas factors of the reduced Hermite system (rows: [2 1], [1 4 1] ..., [1 2])
@@ -217,6 +236,10 @@ int ensure_advect_tables(Handle* H, double tau) {
       if (std::fabs(fl) > 1e6) return fail(H, CHASM_EINVAL, "advection shift too large");
       ns[(size_t)d * nk + j] = (int)fl;
     }
+  for (int d = 0; d < 3; ++d) {
+    H->adv.ns_min[d] = *std::min_element(ns.begin() + (size_t)d * nk, ns.begin() + (size_t)(d + 1) * nk);
+    H->adv.ns_max[d] = *std::max_element(ns.begin() + (size_t)d * nk, ns.begin() + (size_t)(d + 1) * nk);
+  }
   const size_t wbytes = w.size() * H->elt;
   std::vector<unsigned char> blob(wbytes + ns.size() * sizeof(int));
   if (H->fp64)
@@ -358,8 +381,7 @@ void free_all(Handle* H) {
   if (H->stream) cudaStreamSynchronize(H->stream);
   if (H->graph) cudaGraphExecDestroy(H->graph);
   H->graph = nullptr;
-  void* ptrs[] = {H->d_cplus[0], H->d_cplus[1], H->d_cplus[2], H->d_cminus[0], H->d_cminus[1],
-                  H->d_cminus[2], H->d_lu[0], H->d_lu[1], H->d_lu[2], H->adv.dev, H->d_T,
+  void* ptrs[] = {H->d_clos[0], H->d_clos[1], H->d_clos[2], H->d_lu[0], H->d_lu[1], H->d_lu[2], H->adv.dev, H->d_T,
                   H->d_that, H->d_phase, H->d_scratch, H->d_u[0], H->d_u[1], H->d_krows,
                   H->d_partials, H->d_result, H->d_vx, H->d_fhost};
   for (void* p : ptrs)
@@ -466,9 +488,9 @@ size_t chasm_workspace_bytes(const chasm_grid* grid, const chasm_potential* pot,
     cudaGetDevice(&dev);
     int sms = 152;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
-    const int occ = theta_occupancy_blocks(nk, fp64, dev);
-    const int64_t blocks = std::min<int64_t>(nxp, (int64_t)occ * sms);
-    w += theta_scratch_bytes(nk, fp64, (int)blocks);
+    ThetaPlan tp;
+    theta_plan(nk, fp64, nxp, sms, &tp);
+    w += tp.scratch_bytes;
     w += (size_t)8 * nk * nk * nk * e + (size_t)(2 * nk - 1) * (2 * nk - 1) * (2 * nk - 1) * 8;
     w += (size_t)pot->n_nuc * (grid->nx[0] + grid->nx[1] + 4 * grid->nx[2]) * nk * 2 * e;
   }
@@ -562,10 +584,9 @@ int chasm_create(const chasm_grid* grid, const chasm_box* box, const chasm_poten
     if (e != cudaSuccess) return bail(cuda_fail(H, e, "symbol precompute"));
     rc = build_phase_tables(H);
     if (rc) return bail(rc);
-    const int occ = theta_occupancy_blocks(N, H->fp64, H->device);
-    H->theta_blocks = (int)std::min<int64_t>(g.nxp, (int64_t)occ * H->num_sms);
-    const size_t sb = theta_scratch_bytes(N, H->fp64, H->theta_blocks);
-    if (cudaMallocAsync(&H->d_scratch, sb, H->stream) != cudaSuccess ||
+    theta_plan(N, H->fp64, g.nxp, H->num_sms, &H->theta);
+    const size_t sb = H->theta.scratch_bytes;
+    if ((sb > 0 && cudaMallocAsync(&H->d_scratch, sb, H->stream) != cudaSuccess) ||
         cudaMallocAsync(&H->d_u[0], fbytes, H->stream) != cudaSuccess ||
         cudaMallocAsync(&H->d_u[1], fbytes, H->stream) != cudaSuccess)
       return bail(fail(H, CHASM_ENOMEM, "device allocation failed (Horner buffers / scratch)"));

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <algorithm>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -33,6 +34,7 @@ struct AdvectTables {
   double tau = 0.0;
   bool valid = false;
   void* dev = nullptr;      // [3][nk] weights (T x4) followed by [3][nk] int shifts
+  int ns_min[3] = {0, 0, 0}, ns_max[3] = {0, 0, 0};   // range of the integer shifts per dim
 };
 
 struct Handle;
@@ -46,9 +48,12 @@ cudaError_t launch_advect_dim(const Handle& H, void* f, int dim, cudaStream_t s)
 // Coulomb operator (k_theta.cu): out = (base or 0) + sum_a coef[a] * Theta_a[in]
 cudaError_t launch_theta(const Handle& H, const void* in, const void* base, void* out,
                          const double* coef, cudaStream_t s);
-int theta_grid_blocks(const Handle& H);
-size_t theta_scratch_bytes(int nk, bool fp64, int blocks);
-int theta_occupancy_blocks(int nk, bool fp64, int device);
+struct ThetaPlan {
+  int cluster = 0;          // CTAs per cluster of the distributed-shared-memory kernel, 0 = global
+  int blocks = 0;           // grid size (a multiple of cluster)
+  size_t scratch_bytes = 0; // global scratch of the fallback kernel
+};
+void theta_plan(int nk, bool fp64, int64_t nxp, int num_sms, ThetaPlan* plan);
 // symbol precompute (k_symbol.cu): T (FP64, (2N-1)^3) and T-hat (parity-major, scaled)
 cudaError_t compute_symbol(int nk, double lk, double* T_dev, void* that_dev, bool fp64,
                            double* that_absmax_host, cudaStream_t s);
@@ -81,8 +86,9 @@ struct Handle {
 
   // PMBC end stencils (Eq. 3.5) and LU factors of the Hermite-closed system per dimension
   int J[3] = {0, 0, 0};            // stencil lengths min(n_nb, N) + 1
-  double* d_cplus[3] = {nullptr, nullptr, nullptr};
-  double* d_cminus[3] = {nullptr, nullptr, nullptr};
+  // closure coefficients, zero-padded to nx[d] per segment: FP64 [c+ | c-], FP32-mixed
+  // [c+ hi | c+ lo | c- hi | c- lo] (unevaluated float pairs for the compensated dot product)
+  void* d_clos[3] = {nullptr, nullptr, nullptr};
   void* d_lu[3] = {nullptr, nullptr, nullptr};   // [cprime (n) | mult (n)] in storage type
 
   AdvectTables adv;                // current tau tables
@@ -91,8 +97,8 @@ struct Handle {
   void* d_that = nullptr;          // T-hat, storage type, (2N)^3 parity-major, / (2N)^3
   double that_absmax = 0.0;
   void* d_phase = nullptr;         // modulation tables (storage type complex)
-  int theta_blocks = 0;
-  void* d_scratch = nullptr;       // per-CTA scratch of the Theta kernel
+  ThetaPlan theta;                 // launch plan of the Theta kernel
+  void* d_scratch = nullptr;       // per-CTA scratch of the global-scratch Theta kernel
   void* d_u[2] = {nullptr, nullptr};  // Horner buffers
   // harmonic
   void* d_krows = nullptr;         // circulant rows [3][nx_d][nk] for the current dt

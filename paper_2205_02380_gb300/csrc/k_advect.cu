@@ -10,11 +10,19 @@
 //
 // One thread owns one line: fixed k (the contiguous index, so a warp reads 32 consecutive k and
 // every load/store is a coalesced 128-byte (FP32) or 256-byte (FP64) transaction) and fixed
-// other two x indices.  The thread loads its nx values, forms the PMBC closure phi_L, phi_R in
-// FP64, runs the constant-LU Thomas sweep, evaluates the 4-tap stencil and writes the nx new
-// values back over the old ones (no other thread touches the line, so in place is safe).
-// The line lives in shared memory in a column layout (element e of thread t at e*B + t), which
-// is free of bank conflicts.
+// other two x indices.  The thread loads its nx values, forms the PMBC closure phi_L, phi_R, runs
+// the constant-LU Thomas sweep, evaluates the 4-tap stencil and writes the nx new values back
+// over the old ones (no other thread touches the line, so in place is safe).
+//
+// Closure precision.  FP64 form: native FP64.  FP32-mixed form: the closure dot products are
+// accumulated in compensated FP32-pair arithmetic (error-free products by FMA, Knuth's two-sum;
+// about 48 significant bits), i.e. at FP64-class precision without the FP64 pipe, which on GB300
+// delivers 1/64 of the FP32 rate and otherwise bounds this pass.  Everything else is FP32.
+//
+// Two kernels: k_advect_reg keeps the line in registers (line length a compile-time constant
+// from {16, 24, 32, 48, 64} and integer shift in [-2, 1], the usual case since |alpha| < 1);
+// k_advect_smem is the general fallback with the line in shared memory (column layout, element
+// e of thread t at e*B + t, conflict-free).
 #include "internal.hpp"
 
 namespace chasm {
@@ -31,63 +39,176 @@ struct AdvParams {
   int n_b;            // extent of the second "other" dimension
   int kdiv;           // k_d = (kidx / kdiv) % nk
   int nk;
-  int J;              // stencil length
+  int J;              // stencil length (<= n); the coefficient arrays are zero-padded to n
   double h;
-  const double* cplus;
-  const double* cminus;
+  const T* clos;      // closure coefficients (see ClosureFmt)
   const T* cprime;    // Thomas c'_i, i = 0..N
   const T* mult;      // Thomas 1/(b_i - a_i c'_{i-1}), i = 0..N
   const T* w;         // [nk][4] (b4, b3, b2, b1)
   const int* ns;      // [nk] floor(alpha)
 };
 
+// ---- closure accumulators ----
+// FP64: c+ at clos[j], c- at clos[n + j].
+// FP32: c+ hi/lo at clos[j], clos[n + j]; c- hi/lo at clos[2n + j], clos[3n + j].
+struct DF {           // unevaluated sum hi + lo
+  float hi, lo;
+};
+__device__ __forceinline__ void df_acc(DF& s, float x, float chi, float clo) {
+  const float p = x * chi;
+  float e = fmaf(x, chi, -p);          // x * chi = p + e exactly
+  e = fmaf(x, clo, e);
+  const float t = s.hi + p;            // two-sum s.hi + p = t + err
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  s.hi = t;
+  s.lo += err + e;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kAdvectThreads) k_advect_dim(AdvParams<T> p) {
+struct Closure;
+
+template <>
+struct Closure<double> {
+  double L = 0.0, R = 0.0;
+  __device__ __forceinline__ void add(const double* c, int n, int j, double phiL, double phiR) {
+    L = fma(__ldg(c + j), phiL, L);
+    R = fma(__ldg(c + n + j), phiR, R);
+  }
+  // 3 phi_0 + h phi_L, 3 phi_N - h phi_R, and the ghost offsets 2 h phi_L, 2 h phi_R
+  __device__ __forceinline__ double d0(double phi0, double h) const { return 3.0 * phi0 + h * L; }
+  __device__ __forceinline__ double dN(double phiN, double h) const { return 3.0 * phiN - h * R; }
+  __device__ __forceinline__ double gl(double eta1, double h) const { return eta1 - 2.0 * h * L; }
+  __device__ __forceinline__ double gr(double etaNm1, double h) const { return etaNm1 + 2.0 * h * R; }
+};
+
+template <>
+struct Closure<float> {
+  DF L{0.f, 0.f}, R{0.f, 0.f};
+  __device__ __forceinline__ void add(const float* c, int n, int j, float phiL, float phiR) {
+    df_acc(L, phiL, __ldg(c + j), __ldg(c + n + j));
+    df_acc(R, phiR, __ldg(c + 2 * n + j), __ldg(c + 3 * n + j));
+  }
+  __device__ __forceinline__ float d0(float phi0, double h) const {
+    const float hf = (float)h;
+    return fmaf(hf, L.hi, fmaf(hf, L.lo, 3.0f * phi0));
+  }
+  __device__ __forceinline__ float dN(float phiN, double h) const {
+    const float hf = (float)h;
+    return fmaf(-hf, R.hi, fmaf(-hf, R.lo, 3.0f * phiN));
+  }
+  __device__ __forceinline__ float gl(float eta1, double h) const {
+    const float h2 = (float)(2.0 * h);
+    return fmaf(-h2, L.hi, fmaf(-h2, L.lo, eta1));
+  }
+  __device__ __forceinline__ float gr(float etaNm1, double h) const {
+    const float h2 = (float)(2.0 * h);
+    return fmaf(h2, R.hi, fmaf(h2, R.lo, etaNm1));
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void line_setup(const AdvParams<T>& p, int64_t line, T*& src, int& kd) {
+  const int64_t kidx = line % p.kvol;
+  const int64_t outer = line / p.kvol;
+  const int64_t ia = outer / p.n_b, ib = outer % p.n_b;
+  src = p.f + ia * p.s_a + ib * p.s_b + kidx;
+  kd = (int)((kidx / p.kdiv) % p.nk);
+}
+
+// ---- register kernel ----
+template <typename T, int NX, int S>
+__device__ __forceinline__ void eval_store(const T (&v)[NX + 2], T w0, T w1, T w2, T w3, T* src,
+                                           int64_t s_d) {
+  // out_j = w0 eta_{j-S-2} + w1 eta_{j-S-1} + w2 eta_{j-S} + w3 eta_{j-S+1}; slot of eta_nu = nu+1
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    T acc = (T)0;
+    const int s0 = j - S - 1;   // slot of eta_{j-S-2}
+    if (s0 >= 0 && s0 <= NX + 1) acc = w0 * v[s0];
+    if (s0 + 1 >= 0 && s0 + 1 <= NX + 1) acc = fma(w1, v[s0 + 1], acc);
+    if (s0 + 2 >= 0 && s0 + 2 <= NX + 1) acc = fma(w2, v[s0 + 2], acc);
+    if (s0 + 3 >= 0 && s0 + 3 <= NX + 1) acc = fma(w3, v[s0 + 3], acc);
+    src[(int64_t)j * s_d] = acc;
+  }
+}
+
+template <typename T, int NX>
+__global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p) {
+  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= p.n_lines) return;
+  T* src;
+  int kd;
+  line_setup(p, line, src, kd);
+  constexpr int N = NX - 1;
+  T v[NX + 2];   // slot nu + 1 holds eta_nu (phi_j before the solve)
+#pragma unroll
+  for (int j = 0; j < NX; ++j) v[j + 1] = src[(int64_t)j * p.s_d];
+
+  Closure<T> cl;
+#pragma unroll
+  for (int j = 0; j < NX; ++j) cl.add(p.clos, NX, j, v[j + 1], v[N - j + 1]);
+
+  T dp = (T)cl.d0(v[1], p.h) * __ldg(p.mult);
+  v[1] = dp;
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+    dp = ((T)6 * v[i + 1] - dp) * __ldg(p.mult + i);
+    v[i + 1] = dp;
+  }
+  dp = ((T)cl.dN(v[N + 1], p.h) - dp) * __ldg(p.mult + N);
+  v[N + 1] = dp;
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) v[i + 1] = v[i + 1] - __ldg(p.cprime + i) * v[i + 2];
+  v[0] = (T)cl.gl(v[2], p.h);
+  v[N + 2] = (T)cl.gr(v[N], p.h);
+
+  const int sh = __ldg(p.ns + kd);
+  const T w0 = __ldg(p.w + 4 * kd + 0), w1 = __ldg(p.w + 4 * kd + 1);
+  const T w2 = __ldg(p.w + 4 * kd + 2), w3 = __ldg(p.w + 4 * kd + 3);
+  switch (sh) {
+    case -2: eval_store<T, NX, -2>(v, w0, w1, w2, w3, src, p.s_d); break;
+    case -1: eval_store<T, NX, -1>(v, w0, w1, w2, w3, src, p.s_d); break;
+    case 0: eval_store<T, NX, 0>(v, w0, w1, w2, w3, src, p.s_d); break;
+    default: eval_store<T, NX, 1>(v, w0, w1, w2, w3, src, p.s_d); break;
+  }
+}
+
+// ---- shared-memory kernel (any line length, any shift) ----
+template <typename T>
+__global__ void __launch_bounds__(kAdvectThreads) k_advect_smem(AdvParams<T> p) {
   extern __shared__ unsigned char smem_raw[];
   T* buf = reinterpret_cast<T*>(smem_raw) + threadIdx.x;
   const int B = blockDim.x;
   const int64_t line = (int64_t)blockIdx.x * B + threadIdx.x;
   if (line >= p.n_lines) return;
-  const int64_t kidx = line % p.kvol;
-  const int64_t outer = line / p.kvol;
-  const int64_t ia = outer / p.n_b, ib = outer % p.n_b;
-  T* __restrict__ src = p.f + ia * p.s_a + ib * p.s_b + kidx;
-  const int kd = (int)((kidx / p.kdiv) % p.nk);
+  T* src;
+  int kd;
+  line_setup(p, line, src, kd);
   const int n = p.n, N = p.n - 1;
 
-  // load phi_0..phi_N into the slots of eta_0..eta_N (slot of eta_nu is nu + 1)
 #pragma unroll 8
   for (int j = 0; j < n; ++j) buf[(j + 1) * B] = src[(int64_t)j * p.s_d];
 
-  // PMBC closure of the natural-BC global spline (Eq. 3.5), FP64 in both forms
-  double phiL = 0.0, phiR = 0.0;
-  for (int j = 0; j < p.J; ++j) {
-    phiL = fma(__ldg(p.cplus + j), (double)buf[(j + 1) * B], phiL);
-    phiR = fma(__ldg(p.cminus + j), (double)buf[(N - j + 1) * B], phiR);
-  }
+  Closure<T> cl;
+  for (int j = 0; j < p.J; ++j) cl.add(p.clos, n, j, buf[(j + 1) * B], buf[(N - j + 1) * B]);
 
-  // Hermite-closed system with eta_{-1}, eta_{N+1} eliminated:
-  //   2 eta_0 + eta_1 = 3 phi_0 + h phi_L;  eta_{i-1} + 4 eta_i + eta_{i+1} = 6 phi_i;
-  //   eta_{N-1} + 2 eta_N = 3 phi_N - h phi_R.   Constant LU (Thomas) factors from the plan.
-  T dp = (T)(3.0 * (double)buf[B] + p.h * phiL) * __ldg(p.mult);
+  T dp = (T)cl.d0(buf[B], p.h) * __ldg(p.mult);
   buf[B] = dp;
   for (int i = 1; i < N; ++i) {
     dp = ((T)6 * buf[(i + 1) * B] - dp) * __ldg(p.mult + i);
     buf[(i + 1) * B] = dp;
   }
-  dp = ((T)(3.0 * (double)buf[(N + 1) * B] - p.h * phiR) - dp) * __ldg(p.mult + N);
+  dp = ((T)cl.dN(buf[(N + 1) * B], p.h) - dp) * __ldg(p.mult + N);
   buf[(N + 1) * B] = dp;
   T e = dp;
   for (int i = N - 1; i >= 0; --i) {
     e = buf[(i + 1) * B] - __ldg(p.cprime + i) * e;
     buf[(i + 1) * B] = e;
   }
-  // eta_{-1} = eta_1 - 2 h phi_L,  eta_{N+1} = eta_{N-1} + 2 h phi_R   (Eq. 2.12)
-  buf[0] = (T)((double)buf[2 * B] - 2.0 * p.h * phiL);
-  buf[(N + 2) * B] = (T)((double)buf[N * B] + 2.0 * p.h * phiR);
+  buf[0] = (T)cl.gl(buf[2 * B], p.h);
+  buf[(N + 2) * B] = (T)cl.gr(buf[N * B], p.h);
 
-  // 4-tap evaluation at x_j - alpha h: (eta_{j-n-2}, eta_{j-n-1}, eta_{j-n}, eta_{j-n+1}) .
-  // (b4, b3, b2, b1)(alpha - n), n = floor(alpha); coefficients outside [-1, N+1] are zero.
   const int sh = __ldg(p.ns + kd);
   const T w0 = __ldg(p.w + 4 * kd + 0), w1 = __ldg(p.w + 4 * kd + 1);
   const T w2 = __ldg(p.w + 4 * kd + 2), w3 = __ldg(p.w + 4 * kd + 3);
@@ -95,9 +216,9 @@ __global__ void __launch_bounds__(kAdvectThreads) k_advect_dim(AdvParams<T> p) {
     const int nu0 = j - sh - 2;   // first tap index
     T acc = (T)0;
     if (nu0 >= -1 && nu0 <= N + 1) acc = w0 * buf[(nu0 + 1) * B];
-    if (nu0 + 1 >= -1 && nu0 + 1 <= N + 1) acc += w1 * buf[(nu0 + 2) * B];
-    if (nu0 + 2 >= -1 && nu0 + 2 <= N + 1) acc += w2 * buf[(nu0 + 3) * B];
-    if (nu0 + 3 >= -1 && nu0 + 3 <= N + 1) acc += w3 * buf[(nu0 + 4) * B];
+    if (nu0 + 1 >= -1 && nu0 + 1 <= N + 1) acc = fma(w1, buf[(nu0 + 2) * B], acc);
+    if (nu0 + 2 >= -1 && nu0 + 2 <= N + 1) acc = fma(w2, buf[(nu0 + 3) * B], acc);
+    if (nu0 + 3 >= -1 && nu0 + 3 <= N + 1) acc = fma(w3, buf[(nu0 + 4) * B], acc);
     src[(int64_t)j * p.s_d] = acc;
   }
 }
@@ -121,29 +242,39 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
   p.kdiv = dim == 0 ? g.nk * g.nk : (dim == 1 ? g.nk : 1);
   p.J = H.J[dim];
   p.h = g.h[dim];
-  p.cplus = H.d_cplus[dim];
-  p.cminus = H.d_cminus[dim];
+  p.clos = static_cast<const T*>(H.d_clos[dim]);
   p.cprime = static_cast<const T*>(H.d_lu[dim]);
   p.mult = static_cast<const T*>(H.d_lu[dim]) + g.nx[dim];
   const T* wbase = static_cast<const T*>(H.adv.dev);
   p.w = wbase + (size_t)dim * g.nk * 4;
   p.ns = reinterpret_cast<const int*>(wbase + (size_t)3 * g.nk * 4) + dim * g.nk;
   const int B = kAdvectThreads;
+  const unsigned blocks = (unsigned)((p.n_lines + B - 1) / B);
+  const bool reg_shift = H.adv.ns_min[dim] >= -2 && H.adv.ns_max[dim] <= 1;
+  if (reg_shift) {
+    switch (p.n) {
+      case 16: k_advect_reg<T, 16><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
+      case 24: k_advect_reg<T, 24><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
+      case 32: k_advect_reg<T, 32><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
+      case 48: k_advect_reg<T, 48><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
+      case 64: k_advect_reg<T, 64><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
+      default: break;
+    }
+  }
   const size_t smem = (size_t)(g.nx[dim] + 2) * B * sizeof(T);
-  const int64_t blocks = (p.n_lines + B - 1) / B;
-  k_advect_dim<T><<<(unsigned)blocks, B, smem, s>>>(p);
+  k_advect_smem<T><<<blocks, B, smem, s>>>(p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t advect_prepare() {
-  // up to (nx + 2) * 128 * 8 bytes of dynamic shared memory (nx <= 4096 is validated; lines
-  // longer than the shared-memory limit are rejected at create time)
-  cudaError_t e = cudaFuncSetAttribute(k_advect_dim<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // up to (nx + 2) * 128 * sizeof(T) bytes of dynamic shared memory; longer lines are rejected
+  // at create time
+  cudaError_t e = cudaFuncSetAttribute(k_advect_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kAdvectMaxSmem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_advect_dim<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_advect_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               kAdvectMaxSmem);
 }
 

@@ -238,3 +238,29 @@ def test_errors_are_reported_not_raised_on_device(ch):
             s.theta(f, f)                 # aliasing is rejected
         s.step(f, 0.01, 1)                # the handle is still usable
         s.sync()
+
+
+@pytest.mark.parametrize("variant", ["global", "cluster"])
+@pytest.mark.parametrize("name,nk,nx", [("fp32", 32, (4, 5, 4)), ("fp32", 16, (6, 5, 4)),
+                                        ("fp64", 16, (4, 5, 6)), ("fp32", 8, (7, 5, 6))])
+def test_theta_kernel_variants_match_oracle(ch, monkeypatch, variant, name, nk, nx):
+    """Both implementations of the Theta kernel (per-CTA global scratch, and the spectrum held in
+    the shared memory of one CTA or of a thread-block cluster) against the oracle, with two
+    nuclei so the per-nucleus accumulation is exercised."""
+    monkeypatch.setenv("CHASM_THETA_VARIANT", variant)
+    prob = problem(nx, nk, (-2.0, -1.5, -2.5), (2.5, 1.0, 2.0), 4.0,
+                   nuclei=[((0.3, -0.2, 0.1), 1.0), ((-0.4, 0.25, -0.3), 0.7)])
+    f0 = rough_input(prob, 13)
+    with solver(ch, prob, name) as s:
+        u = to_dev(f0, name)
+        out = torch.empty_like(u)
+        s.theta(u, out)
+        base = to_dev(f0 * 0.5, name)
+        s.pflow(base, 0.02)
+        s.sync()
+        got = out.double().cpu().numpy()
+        got_p = base.double().cpu().numpy()
+    ref = O.theta_coulomb(oracle_input(f0, name), prob)
+    assert O.rel_l2(got, ref) <= TOL[name], O.rel_l2(got, ref)
+    ref_p = O.pflow_coulomb(oracle_input(f0 * 0.5, name), prob, 0.02)
+    assert O.rel_l2(got_p, ref_p) <= TOL[name], O.rel_l2(got_p, ref_p)
