@@ -41,6 +41,7 @@ struct AdvParams {
   int nk;
   int J;              // stencil length (<= n); the coefficient arrays are zero-padded to n
   double h;
+  float hf, h2f;      // h and 2h rounded to FP32 (FP32-mixed closure terms)
   const T* clos;      // closure coefficients (see ClosureFmt)
   const T* cprime;    // Thomas c'_i, i = 0..N
   const T* mult;      // Thomas 1/(b_i - a_i c'_{i-1}), i = 0..N
@@ -89,23 +90,33 @@ struct Closure<float> {
     df_acc(L, phiL, __ldg(c + j), __ldg(c + n + j));
     df_acc(R, phiR, __ldg(c + 2 * n + j), __ldg(c + 3 * n + j));
   }
-  __device__ __forceinline__ float d0(float phi0, double h) const {
-    const float hf = (float)h;
+  __device__ __forceinline__ float d0(float phi0, float hf) const {
     return fmaf(hf, L.hi, fmaf(hf, L.lo, 3.0f * phi0));
   }
-  __device__ __forceinline__ float dN(float phiN, double h) const {
-    const float hf = (float)h;
+  __device__ __forceinline__ float dN(float phiN, float hf) const {
     return fmaf(-hf, R.hi, fmaf(-hf, R.lo, 3.0f * phiN));
   }
-  __device__ __forceinline__ float gl(float eta1, double h) const {
-    const float h2 = (float)(2.0 * h);
-    return fmaf(-h2, L.hi, fmaf(-h2, L.lo, eta1));
+  __device__ __forceinline__ float gl(float eta1, float h2f) const {
+    return fmaf(-h2f, L.hi, fmaf(-h2f, L.lo, eta1));
   }
-  __device__ __forceinline__ float gr(float etaNm1, double h) const {
-    const float h2 = (float)(2.0 * h);
-    return fmaf(h2, R.hi, fmaf(h2, R.lo, etaNm1));
+  __device__ __forceinline__ float gr(float etaNm1, float h2f) const {
+    return fmaf(h2f, R.hi, fmaf(h2f, R.lo, etaNm1));
   }
 };
+
+// the h arguments of the closure terms in the storage precision
+template <typename T>
+__device__ __forceinline__ T hval(const AdvParams<T>& p);
+template <>
+__device__ __forceinline__ double hval<double>(const AdvParams<double>& p) { return p.h; }
+template <>
+__device__ __forceinline__ float hval<float>(const AdvParams<float>& p) { return p.hf; }
+template <typename T>
+__device__ __forceinline__ T h2val(const AdvParams<T>& p);
+template <>
+__device__ __forceinline__ double h2val<double>(const AdvParams<double>& p) { return p.h; }
+template <>
+__device__ __forceinline__ float h2val<float>(const AdvParams<float>& p) { return p.h2f; }
 
 template <typename T>
 __device__ __forceinline__ void line_setup(const AdvParams<T>& p, int64_t line, T*& src, int& kd) {
@@ -133,44 +144,69 @@ __device__ __forceinline__ void eval_store(const T (&v)[NX + 2], T w0, T w1, T w
   }
 }
 
+// One line in registers: closure, Thomas sweep, ghosts, 4-tap evaluation and store.
 template <typename T, int NX>
-__global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p) {
-  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (line >= p.n_lines) return;
-  T* src;
-  int kd;
-  line_setup(p, line, src, kd);
+__device__ __forceinline__ void solve_eval_line(const AdvParams<T>& p, T (&v)[NX + 2], int kd, T* dst,
+                                                int64_t s_d) {
   constexpr int N = NX - 1;
-  T v[NX + 2];   // slot nu + 1 holds eta_nu (phi_j before the solve)
-#pragma unroll
-  for (int j = 0; j < NX; ++j) v[j + 1] = src[(int64_t)j * p.s_d];
-
   Closure<T> cl;
 #pragma unroll
   for (int j = 0; j < NX; ++j) cl.add(p.clos, NX, j, v[j + 1], v[N - j + 1]);
 
-  T dp = (T)cl.d0(v[1], p.h) * __ldg(p.mult);
+  T dp = (T)cl.d0(v[1], hval(p)) * __ldg(p.mult);
   v[1] = dp;
 #pragma unroll
   for (int i = 1; i < N; ++i) {
     dp = ((T)6 * v[i + 1] - dp) * __ldg(p.mult + i);
     v[i + 1] = dp;
   }
-  dp = ((T)cl.dN(v[N + 1], p.h) - dp) * __ldg(p.mult + N);
+  dp = ((T)cl.dN(v[N + 1], hval(p)) - dp) * __ldg(p.mult + N);
   v[N + 1] = dp;
 #pragma unroll
   for (int i = N - 1; i >= 0; --i) v[i + 1] = v[i + 1] - __ldg(p.cprime + i) * v[i + 2];
-  v[0] = (T)cl.gl(v[2], p.h);
-  v[N + 2] = (T)cl.gr(v[N], p.h);
+  v[0] = (T)cl.gl(v[2], h2val(p));
+  v[N + 2] = (T)cl.gr(v[N], h2val(p));
 
   const int sh = __ldg(p.ns + kd);
   const T w0 = __ldg(p.w + 4 * kd + 0), w1 = __ldg(p.w + 4 * kd + 1);
   const T w2 = __ldg(p.w + 4 * kd + 2), w3 = __ldg(p.w + 4 * kd + 3);
   switch (sh) {
-    case -2: eval_store<T, NX, -2>(v, w0, w1, w2, w3, src, p.s_d); break;
-    case -1: eval_store<T, NX, -1>(v, w0, w1, w2, w3, src, p.s_d); break;
-    case 0: eval_store<T, NX, 0>(v, w0, w1, w2, w3, src, p.s_d); break;
-    default: eval_store<T, NX, 1>(v, w0, w1, w2, w3, src, p.s_d); break;
+    case -2: eval_store<T, NX, -2>(v, w0, w1, w2, w3, dst, s_d); break;
+    case -1: eval_store<T, NX, -1>(v, w0, w1, w2, w3, dst, s_d); break;
+    case 0: eval_store<T, NX, 0>(v, w0, w1, w2, w3, dst, s_d); break;
+    default: eval_store<T, NX, 1>(v, w0, w1, w2, w3, dst, s_d); break;
+  }
+}
+
+// FP64 form: one line per thread.  FP32-mixed form: two adjacent k (lines l and l + 1 share the
+// x indices) per thread, loaded with 8-byte accesses so each thread keeps twice the bytes in
+// flight.
+template <typename T, int NX>
+__global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p) {
+  constexpr int LPT = sizeof(T) == 4 ? 2 : 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t * LPT >= p.n_lines) return;
+  T* src;
+  int kd;
+  line_setup(p, t * LPT, src, kd);
+  if constexpr (LPT == 1) {
+    T v[NX + 2];   // slot nu + 1 holds eta_nu (phi_j before the solve)
+#pragma unroll
+    for (int j = 0; j < NX; ++j) v[j + 1] = src[(int64_t)j * p.s_d];
+    solve_eval_line<T, NX>(p, v, kd, src, p.s_d);
+  } else {
+    T v0[NX + 2], v1[NX + 2];
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+      const float2 q = *reinterpret_cast<const float2*>(src + (int64_t)j * p.s_d);
+      v0[j + 1] = q.x;
+      v1[j + 1] = q.y;
+    }
+    int kd1;
+    T* src1;
+    line_setup(p, t * LPT + 1, src1, kd1);
+    solve_eval_line<T, NX>(p, v0, kd, src, p.s_d);
+    solve_eval_line<T, NX>(p, v1, kd1, src1, p.s_d);
   }
 }
 
@@ -193,21 +229,21 @@ __global__ void __launch_bounds__(kAdvectThreads) k_advect_smem(AdvParams<T> p) 
   Closure<T> cl;
   for (int j = 0; j < p.J; ++j) cl.add(p.clos, n, j, buf[(j + 1) * B], buf[(N - j + 1) * B]);
 
-  T dp = (T)cl.d0(buf[B], p.h) * __ldg(p.mult);
+  T dp = (T)cl.d0(buf[B], hval(p)) * __ldg(p.mult);
   buf[B] = dp;
   for (int i = 1; i < N; ++i) {
     dp = ((T)6 * buf[(i + 1) * B] - dp) * __ldg(p.mult + i);
     buf[(i + 1) * B] = dp;
   }
-  dp = ((T)cl.dN(buf[(N + 1) * B], p.h) - dp) * __ldg(p.mult + N);
+  dp = ((T)cl.dN(buf[(N + 1) * B], hval(p)) - dp) * __ldg(p.mult + N);
   buf[(N + 1) * B] = dp;
   T e = dp;
   for (int i = N - 1; i >= 0; --i) {
     e = buf[(i + 1) * B] - __ldg(p.cprime + i) * e;
     buf[(i + 1) * B] = e;
   }
-  buf[0] = (T)cl.gl(buf[2 * B], p.h);
-  buf[(N + 2) * B] = (T)cl.gr(buf[N * B], p.h);
+  buf[0] = (T)cl.gl(buf[2 * B], h2val(p));
+  buf[(N + 2) * B] = (T)cl.gr(buf[N * B], h2val(p));
 
   const int sh = __ldg(p.ns + kd);
   const T w0 = __ldg(p.w + 4 * kd + 0), w1 = __ldg(p.w + 4 * kd + 1);
@@ -242,6 +278,8 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
   p.kdiv = dim == 0 ? g.nk * g.nk : (dim == 1 ? g.nk : 1);
   p.J = H.J[dim];
   p.h = g.h[dim];
+  p.hf = (float)g.h[dim];
+  p.h2f = (float)(2.0 * g.h[dim]);
   p.clos = static_cast<const T*>(H.d_clos[dim]);
   p.cprime = static_cast<const T*>(H.d_lu[dim]);
   p.mult = static_cast<const T*>(H.d_lu[dim]) + g.nx[dim];
@@ -252,12 +290,14 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
   const unsigned blocks = (unsigned)((p.n_lines + B - 1) / B);
   const bool reg_shift = H.adv.ns_min[dim] >= -2 && H.adv.ns_max[dim] <= 1;
   if (reg_shift) {
+    const int64_t lpt = sizeof(T) == 4 ? 2 : 1;   // kvol = nk^3 is even
+    const unsigned rblocks = (unsigned)((p.n_lines / lpt + B - 1) / B);
     switch (p.n) {
-      case 16: k_advect_reg<T, 16><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
-      case 24: k_advect_reg<T, 24><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
-      case 32: k_advect_reg<T, 32><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
-      case 48: k_advect_reg<T, 48><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
-      case 64: k_advect_reg<T, 64><<<blocks, B, 0, s>>>(p); return cudaGetLastError();
+      case 16: k_advect_reg<T, 16><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
+      case 24: k_advect_reg<T, 24><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
+      case 32: k_advect_reg<T, 32><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
+      case 48: k_advect_reg<T, 48><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
+      case 64: k_advect_reg<T, 64><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
       default: break;
     }
   }

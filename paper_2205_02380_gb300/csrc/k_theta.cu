@@ -180,13 +180,122 @@ __device__ __forceinline__ void twist(T (&re)[N], T (&im)[N]) {
   }
 }
 
+
+// ---- Phase B building blocks shared by both kernels ----
+// A slab group has GS = 2N threads: lane pair (2 row, 2 row + 1) holds the two frequency
+// parities h = 0, 1 of one padded transform and combines them with warp shuffles, so no thread
+// idles and no parity buffer is needed.  Groups synchronise among themselves only.
+template <int GS>
+__device__ __forceinline__ void group_sync(int grp) {
+  if constexpr (GS <= 32)
+    __syncwarp();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(GS) : "memory");
+}
+
+// Layout of the group's slab buffer V (N rows of the two parity halves of a padded transform):
+// element (row, h, j) at row * VR + h * VH + j with VH = 8 (mod 16) and VR odd, so that the lanes
+// of a half-warp (8 rows x 2 parities) hit 16 different 8-byte banks in every sub-phase.
+template <int N>
+struct VLayout {
+  static constexpr int VH = N >= 16 ? N + 8 : N;
+  static constexpr int VR = VH + N + 1;
+  static constexpr int D = N >= 16 ? 8 : N / 2;   // lane h keeps the elements m with (m / D) % 2 == h
+  __device__ static constexpr int col(int c) { return (c / N) * VH + (c % N); }
+};
+
+// r = mine + partner's (parity partials of the same output vector); lane h stores the elements m
+// with (m / D) % 2 == h of r at dst[m * stride], so the two lanes of a pair write rows D apart.
+template <typename T, int N>
+__device__ __forceinline__ void pair_combine_store(const T (&re)[N], const T (&im)[N], int h,
+                                                   cpx<T>* dst, int stride) {
+  constexpr int D = VLayout<N>::D;
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    const int m0 = (i / D) * 2 * D + (i % D);   // kept by lane 0
+    const int m1 = m0 + D;                      // kept by lane 1
+    const T sre = h ? re[m0] : re[m1];
+    const T sim = h ? im[m0] : im[m1];
+    const T rre = __shfl_xor_sync(0xffffffffu, sre, 1);
+    const T rim = __shfl_xor_sync(0xffffffffu, sim, 1);
+    const T kre = h ? re[m1] : re[m0];
+    const T kim = h ? im[m1] : im[m0];
+    dst[(h ? m1 : m0) * stride] = {kre + rre, kim + rim};
+  }
+}
+
+// The 2-D padded convolution of one slab s3 (fixed k3-frequency) in place: Gs holds the N x N
+// complex k3-spectrum (row stride SR) on entry and Phi's k3-spectrum on exit.  V is the group's
+// N x (2N + 1) complex buffer.  th is T-hat[s3] (parity-major [s1][s2], row length 2N).
+template <typename T, int N, int GS, int SR>
+__device__ __forceinline__ void slab_conv(cpx<T>* Gs, cpx<T>* V, const T* __restrict__ th, int tg,
+                                          int grp) {
+  constexpr int L = 2 * N;
+  using VL = VLayout<N>;
+  const int h = tg & 1, row = tg >> 1;
+  {  // B1: forward along k2 of row k1 = row, parity h
+    T re[N], im[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      const cpx<T> v = Gs[row * SR + n];
+      re[n] = v.re;
+      im[n] = v.im;
+    }
+    if (h) twist<T, N, false>(re, im);
+    fft<T, N, false>(re, im);
+#pragma unroll
+    for (int j = 0; j < N; ++j) V[row * VL::VR + h * VL::VH + j] = {re[j], im[j]};
+  }
+  group_sync<GS>(grp);
+#pragma unroll 1
+  for (int rho = 0; rho < 2; ++rho) {  // B2: column c along k1: forward, x T-hat, inverse
+    const int c = row + N * rho;
+    const int vc = rho * VL::VH + row;
+    T re[N], im[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+      const cpx<T> v = V[n * VL::VR + vc];
+      re[n] = v.re;
+      im[n] = v.im;
+    }
+    if (h) twist<T, N, false>(re, im);
+    fft<T, N, false>(re, im);
+    const T* t = th + (size_t)(h * N) * L + c;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const T w = __ldg(t + (size_t)j * L);
+      re[j] *= w;
+      im[j] *= w;
+    }
+    fft<T, N, true>(re, im);
+    if (h) twist<T, N, true>(re, im);
+    pair_combine_store<T, N>(re, im, h, V + vc, VL::VR);   // column c is read by this pair only
+  }
+  group_sync<GS>(grp);
+  {  // B3: inverse along k2 of row n1 = row, parity h; result back into the slab
+    T re[N], im[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const cpx<T> v = V[row * VL::VR + h * VL::VH + j];
+      re[j] = v.re;
+      im[j] = v.im;
+    }
+    fft<T, N, true>(re, im);
+    if (h) twist<T, N, true>(re, im);
+    pair_combine_store<T, N>(re, im, h, Gs + row * SR, 1);
+  }
+  group_sync<GS>(grp);
+}
+
+// Lines of u, f and the output are touched once per launch: streaming (evict-first) accesses
+// keep them from displacing the per-CTA spectrum scratch and T-hat in L2.
 template <typename T, int N>
 __device__ __forceinline__ void load_line(const T* __restrict__ src, T (&v)[N]) {
   if constexpr (sizeof(T) == 4 && N % 4 == 0) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
     for (int q = 0; q < N / 4; ++q) {
-      const float4 t = s4[q];
+      const float4 t = __ldcs(s4 + q);
       v[4 * q] = t.x;
       v[4 * q + 1] = t.y;
       v[4 * q + 2] = t.z;
@@ -196,7 +305,7 @@ __device__ __forceinline__ void load_line(const T* __restrict__ src, T (&v)[N]) 
     const double2* s2 = reinterpret_cast<const double2*>(src);
 #pragma unroll
     for (int q = 0; q < N / 2; ++q) {
-      const double2 t = s2[q];
+      const double2 t = __ldcs(s2 + q);
       v[2 * q] = (T)t.x;
       v[2 * q + 1] = (T)t.y;
     }
@@ -224,22 +333,22 @@ __device__ __forceinline__ void finish_line(T* __restrict__ o, const T* b, T coe
     const float4* b4 = reinterpret_cast<const float4*>(b);
 #pragma unroll
     for (int q = 0; q < N / 4; ++q) {
-      float4 r = b ? b4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 r = b ? __ldcs(b4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
       r.x += coef * v[4 * q];
       r.y += coef * v[4 * q + 1];
       r.z += coef * v[4 * q + 2];
       r.w += coef * v[4 * q + 3];
-      o4[q] = r;
+      __stcs(o4 + q, r);
     }
   } else {
     double2* o2 = reinterpret_cast<double2*>(o);
     const double2* b2 = reinterpret_cast<const double2*>(b);
 #pragma unroll
     for (int q = 0; q < N / 2; ++q) {
-      double2 r = b ? b2[q] : make_double2(0.0, 0.0);
+      double2 r = b ? __ldcs(b2 + q) : make_double2(0.0, 0.0);
       r.x += coef * v[2 * q];
       r.y += coef * v[2 * q + 1];
-      o2[q] = r;
+      __stcs(o2 + q, r);
     }
   }
 }
@@ -263,11 +372,11 @@ template <int N, int NT_>
 struct ThetaCfg {
   static constexpr int NT = NT_;
   static constexpr int L = 2 * N;
-  static constexpr int GS = 4 * N;         // threads per slab group
+  static constexpr int GS = 2 * N;         // threads per slab group
   static constexpr int NG = NT / GS;       // slab groups per CTA
-  static constexpr int RS = L + 1;         // padded row stride of the slab buffers
-  static_assert(NT % GS == 0 && L % NG == 0, "slab groups must tile the CTA and the slabs");
-  static constexpr int smem_cpx = NG * 2 * N * RS;
+  static constexpr int RS = L + 1;         // padded row stride of the slab buffer
+  static_assert(NT % GS == 0 && (GS <= 32 || NG <= 15), "slab groups must tile the CTA");
+  static constexpr int smem_cpx = NG * N * VLayout<N>::VR;
 };
 
 // Global-scratch kernel: the CTA's 2N^3 complex k3-spectrum lives in a private global scratch
@@ -275,14 +384,13 @@ struct ThetaCfg {
 template <typename T, int N, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_theta(const ThetaParams<T> p) {
   using C = ThetaCfg<N, NT>;
-  constexpr int L = C::L, GS = C::GS, NG = C::NG, RS = C::RS;
+  constexpr int L = C::L, GS = C::GS, NG = C::NG;
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cpx<T>* smem = reinterpret_cast<cpx<T>*>(sm_raw);
   const int tid = threadIdx.x;
   const int grp = tid / GS, tg = tid % GS;
-  cpx<T>* V = smem + grp * (2 * N * RS);
-  cpx<T>* Z = V + N * RS;
+  cpx<T>* V = smem + grp * (N * VLayout<N>::VR);
   cpx<T>* G = p.G + (size_t)blockIdx.x * (2 * N3);
 
   for (int64_t xp = blockIdx.x; xp < p.nxp; xp += gridDim.x) {
@@ -321,79 +429,9 @@ __global__ void __launch_bounds__(NT, MINB) k_theta(const ThetaParams<T> p) {
       __syncthreads();
 
       // ---- Phase B: per slab s3, the 2-D padded convolution in (k1, k2) ----
-      for (int s = grp; s < L; s += NG) {
-        cpx<T>* Gs = G + (size_t)s * N2;
-        for (int e = tg; e < N2; e += GS) Z[(e / N) * (N + 1) + (e % N)] = Gs[e];
-        __syncthreads();
-        if (tg < 2 * N) {  // B1: forward along k2, jobs (r2, k1)
-          const int r2 = tg / N, k1 = tg % N;
-          T re[N], im[N];
-#pragma unroll
-          for (int n = 0; n < N; ++n) {
-            const cpx<T> v = Z[k1 * (N + 1) + n];
-            re[n] = v.re;
-            im[n] = v.im;
-          }
-          if (r2) twist<T, N, false>(re, im);
-          fft<T, N, false>(re, im);
-#pragma unroll
-          for (int j = 0; j < N; ++j) V[k1 * RS + r2 * N + j] = {re[j], im[j]};
-        }
-        __syncthreads();
-        {  // B2: along k1 for column c = (r2, j2): forward, x T-hat, inverse; jobs (r1, c)
-          const int r1 = tg / L, c = tg % L;
-          T re[N], im[N];
-#pragma unroll
-          for (int n = 0; n < N; ++n) {
-            const cpx<T> v = V[n * RS + c];
-            re[n] = v.re;
-            im[n] = v.im;
-          }
-          if (r1) twist<T, N, false>(re, im);
-          fft<T, N, false>(re, im);
-          const T* th = p.that + ((size_t)s * L + r1 * N) * L + c;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const T t = __ldg(th + (size_t)j * L);
-            re[j] *= t;
-            im[j] *= t;
-          }
-          fft<T, N, true>(re, im);
-          if (r1) twist<T, N, true>(re, im);
-          __syncthreads();  // every column of V has been read
-          cpx<T>* dst = r1 ? Z : V;
-#pragma unroll
-          for (int n = 0; n < N; ++n) dst[n * RS + c] = {re[n], im[n]};
-        }
-        __syncthreads();
-        {  // B3: inverse along k2 on V + Z, jobs (r2, n1); parity halves combined through Q
-          T re[N], im[N];
-          const int r2 = tg / N, n1 = tg % N;
-          if (tg < 2 * N) {
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-              const cpx<T> v = V[n1 * RS + r2 * N + j], w = Z[n1 * RS + r2 * N + j];
-              re[j] = v.re + w.re;
-              im[j] = v.im + w.im;
-            }
-            fft<T, N, true>(re, im);
-            if (r2) twist<T, N, true>(re, im);
-          }
-          __syncthreads();
-          cpx<T>* Q = V;  // Q[r2][n1][n2], row stride N + 1 (aliases V and Z)
-          if (tg < 2 * N) {
-#pragma unroll
-            for (int n = 0; n < N; ++n) Q[(r2 * N + n1) * (N + 1) + n] = {re[n], im[n]};
-          }
-          __syncthreads();
-          for (int e = tg; e < N2; e += GS) {
-            const int n1e = e / N, n2e = e % N;
-            const cpx<T> q0 = Q[n1e * (N + 1) + n2e], q1 = Q[(N + n1e) * (N + 1) + n2e];
-            Gs[e] = {q0.re + q1.re, q0.im + q1.im};
-          }
-          __syncthreads();
-        }
-      }
+      for (int s = grp; s < L; s += NG)
+        slab_conv<T, N, GS, N>(G + (size_t)s * N2, V, p.that + (size_t)s * L * L, tg, grp);
+      __syncthreads();
 
       // ---- Phase C: inverse along k3 (both parities), demodulate, Im, write the line ----
       T* P = reinterpret_cast<T*>(smem);   // parity-0 partials, column layout (idle slab buffers)
@@ -447,14 +485,17 @@ template <typename T, int N, int C>
 struct ClCfg {
   static constexpr int NT = 256;
   static constexpr int L = 2 * N;
-  static constexpr int GS = 4 * N;
+  static constexpr int GS = 2 * N;
   static constexpr int NG = NT / GS;
   static constexpr int RS = L + 1;
   static constexpr int SPC = L / C;          // slabs per CTA
   static constexpr int SLAB = N * (N + 1);   // padded slab, complex entries
   static constexpr int KPC = N / C;          // k1 rows per CTA in phases A and C
-  static_assert(NT % GS == 0 && SPC % NG == 0 && N % C == 0, "cluster tiling");
-  static constexpr size_t smem_cpx = (size_t)SPC * SLAB + (size_t)NG * 2 * N * RS;
+  static_assert(NT % GS == 0 && N % C == 0 && (GS <= 32 || NG <= 15), "cluster tiling");
+  // slab buffers; the group buffers also hold the Phase C partials (NT x N reals)
+  static constexpr size_t grp_cpx = (size_t)NG * N * VLayout<N>::VR;
+  static constexpr size_t smem_cpx =
+      (size_t)SPC * SLAB + (grp_cpx * 2 >= (size_t)NT * N ? grp_cpx : ((size_t)NT * N + 1) / 2);
   static constexpr size_t smem_bytes = smem_cpx * sizeof(cpx<T>);
 };
 
@@ -483,15 +524,15 @@ __device__ __forceinline__ void cluster_barrier() {
 template <typename T, int N, int C, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_theta_cl(const ThetaClParams<T> p) {
   using K = ClCfg<T, N, C>;
-  constexpr int L = K::L, GS = K::GS, NG = K::NG, RS = K::RS, NT = K::NT;
+  constexpr int L = K::L, GS = K::GS, NG = K::NG, NT = K::NT;
   constexpr int SPC = K::SPC, SLAB = K::SLAB, KPC = K::KPC;
+  (void)NG;
   constexpr int N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cpx<T>* Gl = reinterpret_cast<cpx<T>*>(sm_raw);
   const int tid = threadIdx.x;
   const int grp = tid / GS, tg = tid % GS;
-  cpx<T>* V = Gl + SPC * SLAB + grp * (2 * N * RS);
-  cpx<T>* Z = V + N * RS;
+  cpx<T>* V = Gl + SPC * SLAB + grp * (N * VLayout<N>::VR);
   int rank = 0;
   cpx<T>* Gr[C];
   if constexpr (C == 1) {
@@ -548,76 +589,8 @@ __global__ void __launch_bounds__(256, MINB) k_theta_cl(const ThetaClParams<T> p
 
       // ---- Phase B: the local slabs, 2-D padded convolution in (k1, k2) ----
       for (int sl = grp; sl < SPC; sl += NG) {
-        const int s = rank * SPC + sl;
-        cpx<T>* Gs = Gl + sl * SLAB;
-        if (tg < 2 * N) {  // B1: forward along k2, jobs (r2, k1)
-          const int r2 = tg / N, k1 = tg % N;
-          T re[N], im[N];
-#pragma unroll
-          for (int n = 0; n < N; ++n) {
-            const cpx<T> v = Gs[k1 * (N + 1) + n];
-            re[n] = v.re;
-            im[n] = v.im;
-          }
-          if (r2) twist<T, N, false>(re, im);
-          fft<T, N, false>(re, im);
-#pragma unroll
-          for (int j = 0; j < N; ++j) V[k1 * RS + r2 * N + j] = {re[j], im[j]};
-        }
-        __syncthreads();
-        {  // B2: along k1: forward, x T-hat, inverse; jobs (r1, c)
-          const int r1 = tg / L, c = tg % L;
-          T re[N], im[N];
-#pragma unroll
-          for (int n = 0; n < N; ++n) {
-            const cpx<T> v = V[n * RS + c];
-            re[n] = v.re;
-            im[n] = v.im;
-          }
-          if (r1) twist<T, N, false>(re, im);
-          fft<T, N, false>(re, im);
-          const T* th = p.that + ((size_t)s * L + r1 * N) * L + c;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const T t = __ldg(th + (size_t)j * L);
-            re[j] *= t;
-            im[j] *= t;
-          }
-          fft<T, N, true>(re, im);
-          if (r1) twist<T, N, true>(re, im);
-          __syncthreads();
-          cpx<T>* dst = r1 ? Z : V;
-#pragma unroll
-          for (int n = 0; n < N; ++n) dst[n * RS + c] = {re[n], im[n]};
-        }
-        __syncthreads();
-        {  // B3: inverse along k2 and parity combine, result back into the slab
-          T re[N], im[N];
-          const int r2 = tg / N, n1 = tg % N;
-          if (tg < 2 * N) {
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-              const cpx<T> v = V[n1 * RS + r2 * N + j], w = Z[n1 * RS + r2 * N + j];
-              re[j] = v.re + w.re;
-              im[j] = v.im + w.im;
-            }
-            fft<T, N, true>(re, im);
-            if (r2) twist<T, N, true>(re, im);
-          }
-          __syncthreads();
-          cpx<T>* Q = V;
-          if (tg < 2 * N) {
-#pragma unroll
-            for (int n = 0; n < N; ++n) Q[(r2 * N + n1) * (N + 1) + n] = {re[n], im[n]};
-          }
-          __syncthreads();
-          for (int e = tg; e < N * N; e += GS) {
-            const int n1e = e / N, n2e = e % N;
-            const cpx<T> q0 = Q[n1e * (N + 1) + n2e], q1 = Q[(N + n1e) * (N + 1) + n2e];
-            Gs[n1e * (N + 1) + n2e] = {q0.re + q1.re, q0.im + q1.im};
-          }
-          __syncthreads();
-        }
+        const int sg = rank * SPC + sl;
+        slab_conv<T, N, GS, N + 1>(Gl + sl * SLAB, V, p.that + (size_t)sg * L * L, tg, grp);
       }
       cluster_barrier<C>();
 
