@@ -138,6 +138,20 @@ def make_solver(ch, precision, stream):
                      precision=precision, stream=stream.cuda_stream)
 
 
+def aggregate_ranks(ms_local: float, cells: int, steps: int, dist=None, device="cpu"):
+    """Max over ranks of the timed milliseconds and the whole-job throughput: every rank updates
+    `cells` cells per step (weak scaling), so value = world * cells * steps / max_ms."""
+    world = 1
+    ms = float(ms_local)
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * cells * steps / (ms / 1e3)
+
+
 def time_steps(torch, s, f, dt, steps, warmup, stream, dist):
     """W untimed steps, then exactly `steps` Strang steps between CUDA events on the solver's
     stream, bracketed by barrier + synchronize.  Returns milliseconds."""
@@ -298,13 +312,8 @@ def run_chasm(args):
             if prec_name == "fp32":
                 clocks = sampler.stop()
             m1, e1 = s.moments(f)
-            ms_t = ms
-            if dist:
-                t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                ms_t = float(t.item())
-            entry = {"ms_per_step": ms_t / steps, "steps": steps,
-                     "value": world * cells * steps / (ms_t / 1e3),
+            ms_t, value = aggregate_ranks(ms, cells, steps, dist, "cuda")
+            entry = {"ms_per_step": ms_t / steps, "steps": steps, "value": value,
                      "mass0": m0, "mass": m1, "energy0": e0, "energy": e1}
             if prec_name == "fp32":
                 reps = 5
@@ -330,6 +339,14 @@ def run_chasm(args):
             torch.cuda.empty_cache()
         result[prec_name] = entry
 
+    accuracy = accuracy_check(torch, ch, stream, args.acc_steps) if rank == 0 else None
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(ch, n_req=16, rate=20.0, seed=2205, nx_choices=(16, 24),
+                              nk_choices=(16,), steps=(10, 30), precisions=(ch.FP32_MIXED,),
+                              budget=150 << 30, max_slots=8, spl=5)
+        serving["sample"] = ("16 requests, Poisson 20/s, nx in {16,24}, nk 16, 10-30 steps, "
+                             "FP32-mixed (the full 64-request stream: bench.py --serve)")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -350,8 +367,8 @@ def run_chasm(args):
                    "l2": "inputs larger than L2 (f = %.1f GB)" % (cells * 4 / 1e9)},
         "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
                  "dtype": "f64"},
-        "mass_drift_rel": {"fp32": (r32["mass"] - r32["mass0"]) / r32["mass0"],
-                           "fp64": (r64["mass"] - r64["mass0"]) / r64["mass0"]},
+        "accuracy": accuracy,
+        "serving": serving,
         "roofline": {"kernel": "k_theta (one Horner stage of P: Theta^T over all x points)",
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
@@ -366,6 +383,112 @@ def run_chasm(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def accuracy_check(torch, ch, stream, steps):
+    """Both forms from the same 1s initial data for `steps` steps: relative L2 of the FP32-mixed
+    result against the FP64 result (the FP64 form is itself pinned to the FP64 oracle) and the
+    relative mass drift of each."""
+    W = WORKLOAD
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, prec, dtp in (("fp64", ch.FP64, torch.float64), ("fp32", ch.FP32_MIXED, torch.float32)):
+            s = make_solver(ch, prec, stream)
+            f = torch.empty((W["nx"],) * 3 + (W["nk"],) * 3, device="cuda", dtype=dtp)
+            s.init_hydrogen_1s(f, n_y=W["n_y"])
+            m0, _ = s.moments(f)
+            s.step(f, W["dt"], steps)
+            m1, _ = s.moments(f)
+            out[name] = (f, (m1 - m0) / m0, m1)
+            s.close()
+        a, b = out["fp32"][0].double(), out["fp64"][0]
+        rel = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        res = {"steps": steps, "rel_l2_fp32_vs_fp64": rel, "tolerance": 1e-5,
+               "mass_rel_diff_fp32_vs_fp64": (out["fp32"][2] - out["fp64"][2]) / out["fp64"][2],
+               "mass_drift_fp32": out["fp32"][1], "mass_drift_fp64": out["fp64"][1],
+               "note": "the FP64 form is pinned to the FP64 oracle at <= 1e-12"}
+        del a, b, out
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
+
+
+def serving_specs(seed, n_req, nx_choices, nk_choices, steps, precisions, L=12.0, lk=4.0):
+    """Seeded request stream: grid from the choices, 1-2 protons uniform in [-2,2]^3 (redrawn when
+    within h/4 of a node), an electron packet with centre in [-4,4]^3 and momentum in [-1.5,1.5]^3,
+    steps uniform in the range, dt = 0.025."""
+    import synth
+    g = synth.SplitMix64(seed)
+    specs = []
+    for i in range(n_req):
+        nx = nx_choices[g.randint(0, len(nx_choices) - 1)]
+        nk = nk_choices[g.randint(0, len(nk_choices) - 1)]
+        h = 2 * L / (nx - 1)
+        nuc = []
+        for _ in range(g.randint(1, 2)):
+            while True:
+                p = [g.uniform(-2, 2) for _ in range(3)]
+                if min(abs((c + L) / h - round((c + L) / h)) for c in p) * h >= h / 4:
+                    break
+            nuc.append((tuple(p), 1.0))
+        pk = [synth.packet([g.uniform(-4, 4) for _ in range(3)],
+                           [g.uniform(-1.5, 1.5) for _ in range(3)])]
+        specs.append(dict(nx=nx, nk=nk, nuclei=nuc, packets=pk,
+                          nsteps=g.randint(steps[0], steps[1]),
+                          precision=precisions[g.randint(0, len(precisions) - 1)],
+                          L=L, lk=lk, dt=0.025))
+    return specs
+
+
+def run_serving(ch, n_req, rate, seed, nx_choices, nk_choices, steps, precisions, budget,
+                max_slots, spl):
+    """Submits the seeded stream with Poisson arrivals (rate per second) to the continuous-
+    batching server and reports latency percentiles and aggregate cell-updates/s."""
+    import synth
+    specs = serving_specs(seed, n_req, nx_choices, nk_choices, steps, precisions)
+    g = synth.SplitMix64(seed + 1)
+    srv = ch.Server(budget, max_slots=max_slots, steps_per_launch=spl, queue_capacity=n_req)
+    try:
+        t0 = time.perf_counter()
+        t_next = 0.0
+        tickets = []
+        for sp in specs:
+            t_next += -math.log(1.0 - g.uniform()) / rate
+            dly = t0 + t_next - time.perf_counter()
+            if dly > 0:
+                time.sleep(dly)
+            req = ch.make_request(sp["nx"], sp["nk"], -sp["L"], sp["L"], sp["lk"], sp["dt"],
+                                  sp["nsteps"], nuclei=sp["nuclei"], packets=sp["packets"],
+                                  precision=sp["precision"])
+            tickets.append(srv.submit(req))
+        res = [srv.wait(t, 3600.0) for t in tickets]
+        wall = time.perf_counter() - t0
+    finally:
+        srv.close()
+    lat = sorted(r.latency_ms for r in res)
+    work = sum(r.cells * r.nsteps for r in res)
+    pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+    return {"requests": len(res), "failed": sum(1 for r in res if r.status != 0),
+            "rate_per_s": rate, "p50_ms": pct(0.50), "p99_ms": pct(0.99),
+            "mean_queue_ms": statistics.mean(r.queue_ms for r in res),
+            "cell_updates_per_s": work / wall, "wall_s": wall}
+
+
+def run_serve_mode(args):
+    """The full serving workload: 64 requests, grids {16,24,32}^3 x {16,32}^3, 10-100 steps,
+    both precisions, HBM budget 150 GB, Poisson arrivals at --rate per second."""
+    import torch
+    import paper_2205_02380_gb300 as ch
+    ch.chasm.lib()
+    out = {"metric": "serving latency and throughput", "unit": "ms / cell-updates/s"}
+    for name, precs in (("fp32", (ch.FP32_MIXED,)), ("fp64", (ch.FP64,)), ("mixed", (ch.FP32_MIXED, ch.FP64))):
+        if args.serve_precisions and name not in args.serve_precisions.split(","):
+            continue
+        out[name] = run_serving(ch, n_req=args.serve_requests, rate=args.rate, seed=2205,
+                                nx_choices=(16, 24, 32), nk_choices=(16, 32),
+                                steps=(10, args.serve_max_steps), precisions=precs,
+                                budget=150 << 30, max_slots=args.slots, spl=5)
+    print(json.dumps(out), flush=True)
 
 
 def run_profile(args):
@@ -396,6 +519,14 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="FP32 timed steps only (no FP64, e2e, baseline or clocks): for ncu captures")
     ap.add_argument("--nx", type=int, default=None, help="override N_x (profiling on smaller cases)")
+    ap.add_argument("--acc-steps", type=int, default=4)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--rate", type=float, default=5.0)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-max-steps", type=int, default=100)
+    ap.add_argument("--serve-precisions", default="")
     ap.add_argument("--sample-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.nx:
@@ -403,6 +534,9 @@ def main():
         WORKLOAD["name"] = WORKLOAD["name"].replace("32^3x32^3", f"{args.nx}^3x32^3")
     if args.profile:
         run_profile(args)
+        return
+    if args.serve:
+        run_serve_mode(args)
         return
     if args.oracle_sample:
         print(json.dumps(oracle_sample(args.sample_seconds)))
