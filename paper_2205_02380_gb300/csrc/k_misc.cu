@@ -177,6 +177,9 @@ struct OneS {
   int64_t xp0, nxl;   // first x point of the chunk and its length
 };
 
+// Folded sample sums.  The FP32-mixed form accumulates the samples in FP32 (the result is stored
+// in FP32), the FP64 form in FP64.
+template <typename R>
 __global__ void k_1s_fold(double2* __restrict__ P, OneS o) {
   const int N = o.nk;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -186,33 +189,42 @@ __global__ void k_1s_fold(double2* __restrict__ P, OneS o) {
   const int r3 = r % N, r2 = (r / N) % N, r1 = r / (N * N);
   const int i3 = (int)(xp % o.nx[2]), i2 = (int)((xp / o.nx[2]) % o.nx[1]);
   const int i1 = (int)(xp / ((int64_t)o.nx[2] * o.nx[1]));
-  const double a1 = o.x_lo[0] + i1 * o.h[0] - o.c[0];
-  const double a2 = o.x_lo[1] + i2 * o.h[1] - o.c[1];
-  const double a3 = o.x_lo[2] + i3 * o.h[2] - o.c[2];
+  const R a1 = (R)(o.x_lo[0] + i1 * o.h[0] - o.c[0]);
+  const R a2 = (R)(o.x_lo[1] + i2 * o.h[1] - o.c[1]);
+  const R a3 = (R)(o.x_lo[2] + i3 * o.h[2] - o.c[2]);
   const int rep = o.ny / N;
-  const double norm = 1.0 / (8.0 * 3.141592653589793 * 3.141592653589793 * 3.141592653589793 *
-                             3.141592653589793);   // (2 sqrt 2 pi^2)^-2
-  double s = 0.0;
+  const R hdy = (R)(0.5 * o.dy);
+  R s = 0;
   for (int b1 = 0; b1 < rep; ++b1) {
-    const double y1 = (double)(r1 + b1 * N - o.ny / 2) * o.dy * 0.5;
-    const double m1 = (a1 - y1) * (a1 - y1), p1 = (a1 + y1) * (a1 + y1);
+    const R y1 = (R)(r1 + b1 * N - o.ny / 2) * hdy;
+    const R m1 = (a1 - y1) * (a1 - y1), p1 = (a1 + y1) * (a1 + y1);
     for (int b2 = 0; b2 < rep; ++b2) {
-      const double y2 = (double)(r2 + b2 * N - o.ny / 2) * o.dy * 0.5;
-      const double m2 = m1 + (a2 - y2) * (a2 - y2), p2 = p1 + (a2 + y2) * (a2 + y2);
+      const R y2 = (R)(r2 + b2 * N - o.ny / 2) * hdy;
+      const R m2 = m1 + (a2 - y2) * (a2 - y2), p2 = p1 + (a2 + y2) * (a2 + y2);
       for (int b3 = 0; b3 < rep; ++b3) {
-        const double y3 = (double)(r3 + b3 * N - o.ny / 2) * o.dy * 0.5;
-        const double rm = sqrt(m2 + (a3 - y3) * (a3 - y3));
-        const double rp = sqrt(p2 + (a3 + y3) * (a3 + y3));
+        const R y3 = (R)(r3 + b3 * N - o.ny / 2) * hdy;
+        const R rm = sqrt(m2 + (a3 - y3) * (a3 - y3));
+        const R rp = sqrt(p2 + (a3 + y3) * (a3 + y3));
         s += exp(-(rm + rp));
       }
     }
   }
-  P[t] = make_double2(s * norm, 0.0);
+  const double norm = 1.0 / (8.0 * 3.141592653589793 * 3.141592653589793 * 3.141592653589793 *
+                             3.141592653589793);   // (2 sqrt 2 pi^2)^-2
+  P[t] = make_double2((double)s * norm, 0.0);
 }
 
-// out[.., j, ..] = sum_r in[.., r, ..] e^{-2 pi i (j - N/2) r / N} along one k axis
+// out[.., j, ..] = sum_r in[.., r, ..] e^{-2 pi i (j - N/2) r / N} along one k axis; the N roots
+// of unity sit in shared memory.
 __global__ void k_1s_dft(const double2* __restrict__ in, double2* __restrict__ out, int64_t nxl,
                          int N, int axis) {
+  __shared__ double2 w[64];
+  if (threadIdx.x < N) {
+    double sn, cs;
+    sincospi(-2.0 * (double)threadIdx.x / N, &sn, &cs);
+    w[threadIdx.x] = make_double2(cs, sn);
+  }
+  __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nxl * N * N * N) return;
   const int64_t cell0 = t - t % ((int64_t)N * N * N);
@@ -220,16 +232,16 @@ __global__ void k_1s_dft(const double2* __restrict__ in, double2* __restrict__ o
   const int stride = axis == 0 ? N * N : (axis == 1 ? N : 1);
   const int j = (e / stride) % N;
   const int64_t lb = cell0 + (e - j * stride);
+  const int js = ((j - N / 2) % N + N) % N;
   double re = 0.0, im = 0.0;
+  int q = 0;
   for (int r = 0; r < N; ++r) {
-    long long q = (long long)(j - N / 2) * r;
-    q %= N;
-    if (q < 0) q += N;
-    double sn, cs;
-    sincospi(-2.0 * (double)q / N, &sn, &cs);
+    const double2 c = w[q];
     const double2 v = in[lb + (int64_t)r * stride];
-    re += v.x * cs - v.y * sn;
-    im += v.x * sn + v.y * cs;
+    re = fma(v.x, c.x, fma(-v.y, c.y, re));
+    im = fma(v.x, c.y, fma(v.y, c.x, im));
+    q += js;
+    if (q >= N) q -= N;
   }
   out[t] = make_double2(re, im);
 }
@@ -327,7 +339,10 @@ cudaError_t launch_init_1s(const Handle& H, void* f, int n_y, const double c[3],
     o.xp0 = x0;
     o.nxl = std::min<int64_t>(chunk, H.g.nxp - x0);
     const int64_t n = o.nxl * kvol;
-    k_1s_fold<<<nblk(n, 128), 128, 0, s>>>(A, o);
+    if (H.fp64)
+      k_1s_fold<double><<<nblk(n, 128), 128, 0, s>>>(A, o);
+    else
+      k_1s_fold<float><<<nblk(n, 128), 128, 0, s>>>(A, o);
     k_1s_dft<<<nblk(n, 256), 256, 0, s>>>(A, B, o.nxl, N, 2);
     k_1s_dft<<<nblk(n, 256), 256, 0, s>>>(B, A, o.nxl, N, 1);
     k_1s_dft<<<nblk(n, 256), 256, 0, s>>>(A, B, o.nxl, N, 0);

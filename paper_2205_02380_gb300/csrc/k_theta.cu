@@ -181,6 +181,55 @@ __device__ __forceinline__ void twist(T (&re)[N], T (&im)[N]) {
 }
 
 
+// ---- scratch accesses with an L2 evict-last policy (the per-CTA spectrum of the global-scratch
+// kernel is rewritten and reread within microseconds; u, f and out stream with evict-first) ----
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> ld_keep(const cpx<T>* p, uint64_t pol);
+template <>
+__device__ __forceinline__ cpx<float> ld_keep<float>(const cpx<float>* p, uint64_t pol) {
+  cpx<float> v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+               : "=f"(v.re), "=f"(v.im)
+               : "l"(p), "l"(pol)
+               : "memory");
+  return v;
+}
+template <>
+__device__ __forceinline__ cpx<double> ld_keep<double>(const cpx<double>* p, uint64_t pol) {
+  cpx<double> v;
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+               : "=d"(v.re), "=d"(v.im)
+               : "l"(p), "l"(pol)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_keep(cpx<float>* p, cpx<float> v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.re), "f"(v.im),
+               "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void st_keep(cpx<double>* p, cpx<double> v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.re), "d"(v.im),
+               "l"(pol)
+               : "memory");
+}
+// slab accessors: shared memory (plain) or global scratch (evict-last)
+template <bool GLOBAL, typename T>
+__device__ __forceinline__ cpx<T> slab_ld(const cpx<T>* p, uint64_t pol) {
+  if constexpr (GLOBAL) return ld_keep<T>(p, pol);
+  else return *p;
+}
+template <bool GLOBAL, typename T>
+__device__ __forceinline__ void slab_st(cpx<T>* p, cpx<T> v, uint64_t pol) {
+  if constexpr (GLOBAL) st_keep(p, v, pol);
+  else *p = v;
+}
+
 // ---- Phase B building blocks shared by both kernels ----
 // A slab group has GS = 2N threads: lane pair (2 row, 2 row + 1) holds the two frequency
 // parities h = 0, 1 of one padded transform and combines them with warp shuffles, so no thread
@@ -206,9 +255,9 @@ struct VLayout {
 
 // r = mine + partner's (parity partials of the same output vector); lane h stores the elements m
 // with (m / D) % 2 == h of r at dst[m * stride], so the two lanes of a pair write rows D apart.
-template <typename T, int N>
+template <typename T, int N, bool GLOBAL = false>
 __device__ __forceinline__ void pair_combine_store(const T (&re)[N], const T (&im)[N], int h,
-                                                   cpx<T>* dst, int stride) {
+                                                   cpx<T>* dst, int stride, uint64_t pol = 0) {
   constexpr int D = VLayout<N>::D;
 #pragma unroll
   for (int i = 0; i < N / 2; ++i) {
@@ -220,16 +269,16 @@ __device__ __forceinline__ void pair_combine_store(const T (&re)[N], const T (&i
     const T rim = __shfl_xor_sync(0xffffffffu, sim, 1);
     const T kre = h ? re[m1] : re[m0];
     const T kim = h ? im[m1] : im[m0];
-    dst[(h ? m1 : m0) * stride] = {kre + rre, kim + rim};
+    slab_st<GLOBAL, T>(dst + (h ? m1 : m0) * stride, {kre + rre, kim + rim}, pol);
   }
 }
 
 // The 2-D padded convolution of one slab s3 (fixed k3-frequency) in place: Gs holds the N x N
 // complex k3-spectrum (row stride SR) on entry and Phi's k3-spectrum on exit.  V is the group's
 // N x (2N + 1) complex buffer.  th is T-hat[s3] (parity-major [s1][s2], row length 2N).
-template <typename T, int N, int GS, int SR>
+template <typename T, int N, int GS, int SR, bool GLOBAL>
 __device__ __forceinline__ void slab_conv(cpx<T>* Gs, cpx<T>* V, const T* __restrict__ th, int tg,
-                                          int grp) {
+                                          int grp, uint64_t pol) {
   constexpr int L = 2 * N;
   using VL = VLayout<N>;
   const int h = tg & 1, row = tg >> 1;
@@ -237,7 +286,7 @@ __device__ __forceinline__ void slab_conv(cpx<T>* Gs, cpx<T>* V, const T* __rest
     T re[N], im[N];
 #pragma unroll
     for (int n = 0; n < N; ++n) {
-      const cpx<T> v = Gs[row * SR + n];
+      const cpx<T> v = slab_ld<GLOBAL, T>(Gs + row * SR + n, pol);
       re[n] = v.re;
       im[n] = v.im;
     }
@@ -282,7 +331,7 @@ __device__ __forceinline__ void slab_conv(cpx<T>* Gs, cpx<T>* V, const T* __rest
     }
     fft<T, N, true>(re, im);
     if (h) twist<T, N, true>(re, im);
-    pair_combine_store<T, N>(re, im, h, Gs + row * SR, 1);
+    pair_combine_store<T, N, GLOBAL>(re, im, h, Gs + row * SR, 1, pol);
   }
   group_sync<GS>(grp);
 }
@@ -374,7 +423,6 @@ struct ThetaCfg {
   static constexpr int L = 2 * N;
   static constexpr int GS = 2 * N;         // threads per slab group
   static constexpr int NG = NT / GS;       // slab groups per CTA
-  static constexpr int RS = L + 1;         // padded row stride of the slab buffer
   static_assert(NT % GS == 0 && (GS <= 32 || NG <= 15), "slab groups must tile the CTA");
   static constexpr int smem_cpx = NG * N * VLayout<N>::VR;
 };
@@ -392,6 +440,7 @@ __global__ void __launch_bounds__(NT, MINB) k_theta(const ThetaParams<T> p) {
   const int grp = tid / GS, tg = tid % GS;
   cpx<T>* V = smem + grp * (N * VLayout<N>::VR);
   cpx<T>* G = p.G + (size_t)blockIdx.x * (2 * N3);
+  const uint64_t pol = l2_keep_policy();
 
   for (int64_t xp = blockIdx.x; xp < p.nxp; xp += gridDim.x) {
     const int i3 = (int)(xp % p.nx3);
@@ -424,13 +473,13 @@ __global__ void __launch_bounds__(NT, MINB) k_theta(const ThetaParams<T> p) {
         fft<T, N, false>(re, im);
         cpx<T>* g = G + (size_t)(r3 * N) * N2 + line;
 #pragma unroll
-        for (int j = 0; j < N; ++j) g[(size_t)j * N2] = {re[j], im[j]};
+        for (int j = 0; j < N; ++j) st_keep(g + (size_t)j * N2, cpx<T>{re[j], im[j]}, pol);
       }
       __syncthreads();
 
       // ---- Phase B: per slab s3, the 2-D padded convolution in (k1, k2) ----
       for (int s = grp; s < L; s += NG)
-        slab_conv<T, N, GS, N>(G + (size_t)s * N2, V, p.that + (size_t)s * L * L, tg, grp);
+        slab_conv<T, N, GS, N, true>(G + (size_t)s * N2, V, p.that + (size_t)s * L * L, tg, grp, pol);
       __syncthreads();
 
       // ---- Phase C: inverse along k3 (both parities), demodulate, Im, write the line ----
@@ -444,7 +493,7 @@ __global__ void __launch_bounds__(NT, MINB) k_theta(const ThetaParams<T> p) {
           const cpx<T>* g = G + (size_t)(r3 * N) * N2 + line;
 #pragma unroll
           for (int j = 0; j < N; ++j) {
-            const cpx<T> v = g[(size_t)j * N2];
+            const cpx<T> v = ld_keep<T>(g + (size_t)j * N2, pol);
             re[j] = v.re;
             im[j] = v.im;
           }
@@ -590,7 +639,7 @@ __global__ void __launch_bounds__(256, MINB) k_theta_cl(const ThetaClParams<T> p
       // ---- Phase B: the local slabs, 2-D padded convolution in (k1, k2) ----
       for (int sl = grp; sl < SPC; sl += NG) {
         const int sg = rank * SPC + sl;
-        slab_conv<T, N, GS, N + 1>(Gl + sl * SLAB, V, p.that + (size_t)sg * L * L, tg, grp);
+        slab_conv<T, N, GS, N + 1, false>(Gl + sl * SLAB, V, p.that + (size_t)sg * L * L, tg, grp, 0);
       }
       cluster_barrier<C>();
 
