@@ -13,8 +13,8 @@
 // T_m = (3N)^-3 sum_n U prod_d cos(2 pi m_d n_d / 3N), evaluated as three separable passes.
 // T-hat is real and even likewise: T-hat_xi = sum_{m_d >= 0} T_m prod_d w(m_d) cos(pi xi_d m_d/N)
 // with w(0) = 1, w(m > 0) = 2, again three separable passes.  The result is written in the
-// parity-major order of the Theta kernel (s = (xi mod 2) N + xi / 2 per dimension), scaled by
-// 1/(2N)^3, in the storage precision.
+// parity-major order of the Theta kernel (s = (xi mod 2) N + xi / 2 per dimension), as
+// [s3][s1][s2], scaled by 1/(2N)^3, in the storage precision.
 #include <cmath>
 #include <vector>
 

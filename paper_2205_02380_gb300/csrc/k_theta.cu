@@ -89,6 +89,29 @@ __constant__ double c_sin64d[64] = {CHASM_C64(ce_sin2pi)};
 __constant__ float c_cos64f[64] = {CHASM_C64((float)ce_cos2pi)};
 __constant__ float c_sin64f[64] = {CHASM_C64((float)ce_sin2pi)};
 
+// FMA-form butterfly constants (Linzer and Feig, "Modified FFTs for fused multiply-add
+// architectures", Math. Comp. 1993): the twiddle w = cos + i sin is written as m (1 + i r) or
+// m (r + i) with |r| <= 1, so that a +- w x costs six FMAs.  big(k): |cos| >= |sin|.
+__host__ __device__ constexpr bool lf_big(int k) { return (k % 32) <= 8 || (k % 32) >= 24; }
+constexpr double lf_ratio(int k, int n) {
+  return lf_big(k) ? ce_sin2pi(k, n) / ce_cos2pi(k, n) : ce_cos2pi(k, n) / ce_sin2pi(k, n);
+}
+constexpr double lf_scale(int k, int n) { return lf_big(k) ? ce_cos2pi(k, n) : ce_sin2pi(k, n); }
+__constant__ double c_lfr64d[64] = {CHASM_C64(lf_ratio)};
+__constant__ double c_lfm64d[64] = {CHASM_C64(lf_scale)};
+__constant__ float c_lfr64f[64] = {CHASM_C64((float)lf_ratio)};
+__constant__ float c_lfm64f[64] = {CHASM_C64((float)lf_scale)};
+template <typename T>
+__device__ __forceinline__ T lf_r(int k) {
+  if constexpr (sizeof(T) == 4) return c_lfr64f[k];
+  else return c_lfr64d[k];
+}
+template <typename T>
+__device__ __forceinline__ T lf_m(int k) {
+  if constexpr (sizeof(T) == 4) return c_lfm64f[k];
+  else return c_lfm64d[k];
+}
+
 template <typename T>
 __device__ __forceinline__ T tw_cos(int k);
 template <typename T>
@@ -136,32 +159,39 @@ __device__ __forceinline__ void fft(T (&re)[N], T (&im)[N]) {
 #pragma unroll
       for (int i = j; i < N; i += 2 * half) {
         const T xr = re[i + half], xi = im[i + half];
-        T tr, ti;
-        if (k64 == 0) {
-          tr = xr;
-          ti = xi;
-        } else if (k64 == 16) {
-          if (!INV) {
+        if (k64 == 0 || k64 == 16) {
+          T tr, ti;   // w = 1, or w = -i (forward) / +i (inverse)
+          if (k64 == 0) {
+            tr = xr;
+            ti = xi;
+          } else if (!INV) {
             tr = xi;
             ti = -xr;
           } else {
             tr = -xi;
             ti = xr;
           }
+          re[i + half] = re[i] - tr;
+          im[i + half] = im[i] - ti;
+          re[i] += tr;
+          im[i] += ti;
         } else {
-          const T c = tw_cos<T>(k64), s = tw_sin<T>(k64);
-          if (!INV) {
-            tr = xr * c + xi * s;
-            ti = xi * c - xr * s;
+          // w = cos -+ i sin = m (1 + i r) (big) or m (r + i); w x = m (p + i q)
+          const T r = INV ? lf_r<T>(k64) : -lf_r<T>(k64);
+          const T m = (lf_big(k64) || INV) ? lf_m<T>(k64) : -lf_m<T>(k64);
+          T pr, qi;
+          if (lf_big(k64)) {
+            pr = fma(-xi, r, xr);
+            qi = fma(xr, r, xi);
           } else {
-            tr = xr * c - xi * s;
-            ti = xi * c + xr * s;
+            pr = fma(xr, r, -xi);
+            qi = fma(xi, r, xr);
           }
+          re[i + half] = fma(-m, pr, re[i]);
+          re[i] = fma(m, pr, re[i]);
+          im[i + half] = fma(-m, qi, im[i]);
+          im[i] = fma(m, qi, im[i]);
         }
-        re[i + half] = re[i] - tr;
-        im[i + half] = im[i] - ti;
-        re[i] += tr;
-        im[i] += ti;
       }
     }
   }
@@ -218,16 +248,17 @@ __device__ __forceinline__ void st_keep(cpx<double>* p, cpx<double> v, uint64_t 
                "l"(pol)
                : "memory");
 }
-// slab accessors: shared memory (plain) or global scratch (evict-last)
-template <bool GLOBAL, typename T>
-__device__ __forceinline__ cpx<T> slab_ld(const cpx<T>* p, uint64_t pol) {
-  if constexpr (GLOBAL) return ld_keep<T>(p, pol);
-  else return *p;
+// two adjacent single-precision complex values per access (16-byte aligned)
+__device__ __forceinline__ void ld2_keep(const cpx<float>* p, uint64_t pol, cpx<float>& a, cpx<float>& b) {
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(a.re), "=f"(a.im), "=f"(b.re), "=f"(b.im)
+               : "l"(p), "l"(pol)
+               : "memory");
 }
-template <bool GLOBAL, typename T>
-__device__ __forceinline__ void slab_st(cpx<T>* p, cpx<T> v, uint64_t pol) {
-  if constexpr (GLOBAL) st_keep(p, v, pol);
-  else *p = v;
+__device__ __forceinline__ void st2_keep(cpx<float>* p, cpx<float> a, cpx<float> b, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(a.re),
+               "f"(a.im), "f"(b.re), "f"(b.im), "l"(pol)
+               : "memory");
 }
 
 // ---- Phase B building blocks shared by both kernels ----
@@ -269,7 +300,36 @@ __device__ __forceinline__ void pair_combine_store(const T (&re)[N], const T (&i
     const T rim = __shfl_xor_sync(0xffffffffu, sim, 1);
     const T kre = h ? re[m1] : re[m0];
     const T kim = h ? im[m1] : im[m0];
-    slab_st<GLOBAL, T>(dst + (h ? m1 : m0) * stride, {kre + rre, kim + rim}, pol);
+    if constexpr (GLOBAL)
+      st_keep(dst + (h ? m1 : m0) * stride, {kre + rre, kim + rim}, pol);
+    else
+      dst[(h ? m1 : m0) * stride] = {kre + rre, kim + rim};
+  }
+}
+
+// The same into a contiguous single-precision global row (stride 1): the two elements m, m + 1 a
+// lane keeps are written by one 16-byte store.
+template <int N>
+__device__ __forceinline__ void pair_combine_store_row(const float (&re)[N], const float (&im)[N],
+                                                       int h, cpx<float>* dst, uint64_t pol) {
+  constexpr int D = VLayout<N>::D;
+  static_assert(D % 2 == 0, "element pairs stay within a lane's run");
+#pragma unroll
+  for (int i = 0; i < N / 2; i += 2) {
+    const int m0 = (i / D) * 2 * D + (i % D);
+    const int m1 = m0 + D;
+    cpx<float> r[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float sre = h ? re[m0 + e] : re[m1 + e];
+      const float sim = h ? im[m0 + e] : im[m1 + e];
+      const float rre = __shfl_xor_sync(0xffffffffu, sre, 1);
+      const float rim = __shfl_xor_sync(0xffffffffu, sim, 1);
+      const float kre = h ? re[m1 + e] : re[m0 + e];
+      const float kim = h ? im[m1 + e] : im[m0 + e];
+      r[e] = {kre + rre, kim + rim};
+    }
+    st2_keep(dst + (h ? m1 : m0), r[0], r[1], pol);
   }
 }
 
@@ -285,10 +345,21 @@ __device__ __forceinline__ void slab_conv(cpx<T>* Gs, cpx<T>* V, const T* __rest
   {  // B1: forward along k2 of row k1 = row, parity h
     T re[N], im[N];
 #pragma unroll
-    for (int n = 0; n < N; ++n) {
-      const cpx<T> v = slab_ld<GLOBAL, T>(Gs + row * SR + n, pol);
-      re[n] = v.re;
-      im[n] = v.im;
+    for (int n = 0; n < N; n += 2) {
+      cpx<T> a, b;
+      if constexpr (GLOBAL && sizeof(T) == 4) {
+        ld2_keep(Gs + row * SR + n, pol, a, b);
+      } else if constexpr (GLOBAL) {
+        a = ld_keep<T>(Gs + row * SR + n, pol);
+        b = ld_keep<T>(Gs + row * SR + n + 1, pol);
+      } else {
+        a = Gs[row * SR + n];
+        b = Gs[row * SR + n + 1];
+      }
+      re[n] = a.re;
+      im[n] = a.im;
+      re[n + 1] = b.re;
+      im[n + 1] = b.im;
     }
     if (h) twist<T, N, false>(re, im);
     fft<T, N, false>(re, im);
@@ -331,7 +402,10 @@ __device__ __forceinline__ void slab_conv(cpx<T>* Gs, cpx<T>* V, const T* __rest
     }
     fft<T, N, true>(re, im);
     if (h) twist<T, N, true>(re, im);
-    pair_combine_store<T, N, GLOBAL>(re, im, h, Gs + row * SR, 1, pol);
+    if constexpr (GLOBAL && sizeof(T) == 4)
+      pair_combine_store_row<N>(re, im, h, Gs + row * SR, pol);
+    else
+      pair_combine_store<T, N, GLOBAL>(re, im, h, Gs + row * SR, 1, pol);
   }
   group_sync<GS>(grp);
 }
@@ -536,7 +610,6 @@ struct ClCfg {
   static constexpr int L = 2 * N;
   static constexpr int GS = 2 * N;
   static constexpr int NG = NT / GS;
-  static constexpr int RS = L + 1;
   static constexpr int SPC = L / C;          // slabs per CTA
   static constexpr int SLAB = N * (N + 1);   // padded slab, complex entries
   static constexpr int KPC = N / C;          // k1 rows per CTA in phases A and C
