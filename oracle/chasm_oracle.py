@@ -414,24 +414,48 @@ def pflow_coulomb(f: np.ndarray, prob: Problem, dt: float, T: np.ndarray | None 
     return u
 
 
-def pflow_harmonic(f: np.ndarray, prob: Problem, dt: float) -> np.ndarray:
-    """P(dt) for V = kappa/2 |x - c|^2: Theta = (1/hbar) grad V . grad_k f exactly (Eq. 5.1), so
-    the flow is the shift f(x, k + dt kappa (x - c)/hbar).  Applied spectrally per k-axis on the
-    periodic k-grid: multiply mode xi_m = pi m / L_k, m in [-N_k/2, N_k/2), by e^{i xi_m s}, with
-    the Nyquist factor cos(xi s) so the result stays real."""
+def _kshift_factors(prob: Problem, d: int, dt: float) -> np.ndarray:
+    """Per (x_d index, k_d mode in FFT order) factor of the exact k-shift by
+    s = dt kappa (x_d - c_d)/hbar (Eq. 5.1): e^{i xi_m s}, xi_m = pi m / L_k, m in [-N_k/2, N_k/2),
+    with cos(xi s) at the Nyquist mode so the result stays real."""
     nk = prob.nk
     m = np.fft.fftfreq(nk, d=1.0 / nk)          # integer modes in FFT order, -N/2 at slot N/2
     xi = math.pi * m / prob.lk
+    s = dt * prob.kappa * (prob.xs(d) - prob.center[d]) / prob.hbar   # shift per x_d
+    fac = np.exp(1j * xi[None, :] * s[:, None])
+    fac[:, nk // 2] = np.cos(xi[nk // 2] * s)
+    return fac
+
+
+def pflow_harmonic(f: np.ndarray, prob: Problem, dt: float) -> np.ndarray:
+    """P(dt) for V = kappa/2 |x - c|^2: Theta = (1/hbar) grad V . grad_k f exactly (Eq. 5.1), so
+    the flow is the shift f(x, k + dt kappa (x - c)/hbar).  Applied spectrally per k-axis on the
+    periodic k-grid (factors from _kshift_factors)."""
+    nk = prob.nk
     F = np.fft.fftn(f, axes=(3, 4, 5))
     for d in range(3):
-        s = dt * prob.kappa * (prob.xs(d) - prob.center[d]) / prob.hbar   # shift per x_d
-        fac = np.exp(1j * xi[None, :] * s[:, None])
-        fac[:, nk // 2] = np.cos(xi[nk // 2] * s)
         shape = [1] * 6
         shape[d] = prob.nx[d]
         shape[3 + d] = nk
-        F = F * fac.reshape(shape)
+        F = F * _kshift_factors(prob, d, dt).reshape(shape)
     return np.real(np.fft.ifftn(F, axes=(3, 4, 5)))
+
+
+def strang_step_plane(g: np.ndarray, prob: Problem, d: int, dt: float) -> np.ndarray:
+    """One Strang step of the quadratic-potential scheme on the (x_d, k_d) plane, g[i, j] at
+    (x_{d,i}, k_j).
+
+    For V = kappa/2 |x - c|^2 both substeps act on each pair (x_d, k_d) separately: A(tau) is the
+    product over d of 1-D spline interpolations along x_d with shifts set by k_d (Eqs. 3.9, 3.10)
+    and P(dt) the product over d of shifts along k_d by dt kappa (x_d - c_d)/hbar (Eq. 5.1).  A
+    product f = prod_d g_d(x_d, k_d) is therefore mapped factor by factor, and this function is
+    the factor map (it calls the same 1-D spline and k-shift as the 6-D step)."""
+    def a_half(gg):
+        alpha = prob.hbar * prob.ks() * (0.5 * dt) / (prob.m * prob.hs(d))
+        return advect_1d(gg, 0, prob.hs(d), prob.n_nb, alpha, 1)
+    g = a_half(g)
+    g = np.real(np.fft.ifft(np.fft.fft(g, axis=1) * _kshift_factors(prob, d, dt), axis=1))
+    return a_half(g)
 
 
 def pflow(f: np.ndarray, prob: Problem, dt: float, T=None) -> np.ndarray:

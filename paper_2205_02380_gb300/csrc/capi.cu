@@ -217,6 +217,23 @@ int build_spline_plan(Handle* H) {
 
 // Advection weights for A(tau): alpha = hbar k tau / (m h_d), n = floor(alpha), a = alpha - n,
 // (b4, b3, b2, b1)(a) of Eq. 3.7 (reading for any sign and size of alpha: shift by n nodes).
+// Rounds n weights whose exact sum is 1 to FP32 and then resets the one of smallest magnitude
+// to 1 minus the (exact) sum of the others, so the stored weights still form a partition of
+// unity.  Otherwise the rounding of the same weights, applied at every pass, shifts the mass by
+// up to a few 1e-8 per pass in one direction (for alpha = 0: fl(1/6) + fl(2/3) + fl(1/6) =
+// 1 + 3e-8).
+static void round_unit_sum(const double* w, float* out, int n) {
+  int jmin = 0;
+  for (int i = 0; i < n; ++i) {
+    out[i] = (float)w[i];
+    if (std::fabs(out[i]) < std::fabs(out[jmin])) jmin = i;
+  }
+  double rest = 0.0;
+  for (int i = 0; i < n; ++i)
+    if (i != jmin) rest += (double)out[i];
+  out[jmin] = (float)(1.0 - rest);
+}
+
 int ensure_advect_tables(Handle* H, double tau) {
   if (H->adv.valid && H->adv.tau == tau) return CHASM_OK;
   const int nk = H->g.nk;
@@ -245,7 +262,8 @@ int ensure_advect_tables(Handle* H, double tau) {
   if (H->fp64)
     std::memcpy(blob.data(), w.data(), wbytes);
   else {
-    std::vector<float> wf(w.begin(), w.end());
+    std::vector<float> wf(w.size());
+    for (size_t q = 0; q < w.size(); q += 4) round_unit_sum(&w[q], &wf[q], 4);
     std::memcpy(blob.data(), wf.data(), wbytes);
   }
   std::memcpy(blob.data() + wbytes, ns.data(), ns.size() * sizeof(int));
@@ -283,7 +301,16 @@ int ensure_kshift_rows(Handle* H, double dt) {
         rows[(size_t)id * N + q] = acc / N;
       }
     }
-  int rc = upload_real(H, &H->d_krows, rows);
+  int rc;
+  if (H->fp64) {
+    rc = upload_real(H, &H->d_krows, rows);
+  } else {   // the columns of the circulant sum to 1: keep that in FP32 (mass of the k-shift)
+    std::vector<float> rf(rows.size());
+    for (int r = 0; r < tot; ++r) round_unit_sum(&rows[(size_t)r * N], &rf[(size_t)r * N], N);
+    rc = upload(H, &H->d_krows, rf.data(), rf.size() * sizeof(float));
+    if (rc == CHASM_OK && cudaStreamSynchronize(H->stream) != cudaSuccess)
+      rc = fail(H, CHASM_ECUDA, "k-shift table upload");
+  }
   if (rc) return rc;
   H->krows_dt = dt;
   H->krows_valid = true;
