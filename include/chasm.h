@@ -53,6 +53,20 @@ enum {
 
 enum { CHASM_FP32_MIXED = 0, CHASM_FP64 = 1 };
 
+/* How the Coulomb operator Theta^T is evaluated (chasm_options.theta_form).  Both forms compute
+ * the same truncated-kernel convolution (Eqs. 4.1, 4.5-4.7) and agree to rounding.
+ *   CHASM_THETA_TABLE: the real form.  For each x point Theta^T[u] = sum_q S_{p-q}(x) u_q with the
+ *     real, odd kernel S_m(x) = sum_A -(2 Z_A/(pi^2 hbar)) T_m sin(2 (x - x_A) . m dk); chasm_create
+ *     tabulates the spectrum of S for every x point (4 N_k^3 values per x point, i.e. four copies
+ *     of f) and each application then costs one real padded convolution for all nuclei together
+ *     (half the FFT work of one nucleus in the modulated form).  P(dt) runs its four Horner
+ *     stages per x point in one kernel and needs no Horner buffers.
+ *   CHASM_THETA_MODULATED: the complex form of Eq. 4.6 per nucleus (modulate by e^{-2i(x-x_A).k},
+ *     convolve with T, demodulate, imaginary part); workspace two copies of f.
+ *   CHASM_THETA_AUTO (default): the table form when the table needs at most 64 GiB, else the
+ *     modulated form. */
+enum { CHASM_THETA_AUTO = 0, CHASM_THETA_TABLE = 1, CHASM_THETA_MODULATED = 2 };
+
 /* Grid: points per dimension.  nx[d] >= 4; nk[0] = nk[1] = nk[2] in {8, 16, 32}. */
 typedef struct {
   int32_t nx[3];
@@ -88,6 +102,7 @@ typedef struct {
   int32_t patches[3];   /* patches per x-dimension p (Sec. 3.1); only p = 1 is implemented  */
   int32_t use_graphs;   /* 1 (default): chasm_step replays a captured CUDA graph per step   */
   void* cuda_stream;    /* cudaStream_t to run on; NULL: the handle creates its own stream  */
+  int32_t theta_form;   /* CHASM_THETA_AUTO (default), CHASM_THETA_TABLE, CHASM_THETA_MODULATED */
 } chasm_options;
 
 /* One initial wavepacket w exp(-ax |x - x0|^2 - ak |k - k0|^2). */
@@ -119,9 +134,10 @@ int chasm_destroy(chasm_handle* h);
 /* Last error message of this handle (or of the calling thread when h == NULL). */
 const char* chasm_last_error(const chasm_handle* h);
 
-/* Device bytes the handle allocates besides the caller's f: two Horner buffers (Coulomb only),
- * the per-CTA FFT scratch of the Theta kernel, the symbol and small tables.  0 on invalid
- * arguments. */
+/* Device bytes the handle allocates besides the caller's f, for Coulomb potentials: in the table
+ * form the per-x symbol table (4 N_k^3 elements per x point), in the modulated form two Horner
+ * buffers; in both the per-CTA FFT scratch of the Theta kernel, the symbol T, T-hat and small
+ * tables.  0 on invalid arguments. */
 size_t chasm_workspace_bytes(const chasm_grid* grid, const chasm_potential* pot,
                              const chasm_options* opt);
 

@@ -2,4 +2,5 @@
 (Xiong, Zhang, Shao, arXiv 2205.02380): CUDA kernels behind the C ABI of include/chasm.h, with a
 ctypes binding in ``chasm``."""
 from . import chasm  # noqa: F401
-from .chasm import FP32_MIXED, FP64, ChasmError, Server, Solver, make_request  # noqa: F401
+from .chasm import (FP32_MIXED, FP64, THETA_AUTO, THETA_MODULATED, THETA_TABLE,  # noqa: F401
+                    ChasmError, Server, Solver, make_request)

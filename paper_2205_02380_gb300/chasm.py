@@ -13,6 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libchasm.so")
 
 OK, PENDING = 0, 1
+THETA_AUTO, THETA_TABLE, THETA_MODULATED = 0, 1, 2
 EINVAL, ENOMEM, ECUDA, EUNSTABLE, EBUSY, EAGAIN, ETIMEOUT, ENOTFOUND, ECANCELED = (
     -1, -2, -3, -4, -5, -6, -7, -8, -9)
 FP32_MIXED, FP64 = 0, 1
@@ -43,7 +44,7 @@ class Potential(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("n_nb", C.c_int32), ("patches", C.c_int32 * 3),
-                ("use_graphs", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("use_graphs", C.c_int32), ("cuda_stream", C.c_void_p), ("theta_form", C.c_int32)]
 
 
 class Gaussian(C.Structure):
@@ -163,7 +164,8 @@ class Solver:
     results are visible to torch work issued after the call (device-side dependencies only)."""
 
     def __init__(self, nx, nk, x_lo, x_hi, lk, nuclei=(), kappa=0.0, center=(0.0, 0.0, 0.0),
-                 hbar=1.0, m=1.0, precision=FP32_MIXED, n_nb=20, use_graphs=True, stream=None):
+                 hbar=1.0, m=1.0, precision=FP32_MIXED, n_nb=20, use_graphs=True, stream=None,
+                 theta_form=THETA_AUTO):
         L = lib()
         self._tstream = None
         if stream is None:
@@ -186,6 +188,7 @@ class Solver:
         opt.n_nb = n_nb
         opt.use_graphs = 1 if use_graphs else 0
         opt.cuda_stream = stream if stream is not None else None
+        opt.theta_form = theta_form
         self.opt = opt
         h = C.c_void_p()
         _check(L.chasm_create(C.byref(self.grid), C.byref(self.box), C.byref(self.pot), hbar, m,
@@ -288,7 +291,8 @@ class Solver:
         return m.value
 
 
-def workspace_bytes(nx, nk, nuclei=(), kappa=0.0, precision=FP32_MIXED, n_nb=20) -> int:
+def workspace_bytes(nx, nk, nuclei=(), kappa=0.0, precision=FP32_MIXED, n_nb=20,
+                    theta_form=THETA_AUTO) -> int:
     L = lib()
     g = make_grid(nx, nk)
     nuc = (Nucleus * max(1, len(nuclei)))(*[Nucleus((C.c_double * 3)(*p), z) for p, z in nuclei])
@@ -297,6 +301,7 @@ def workspace_bytes(nx, nk, nuclei=(), kappa=0.0, precision=FP32_MIXED, n_nb=20)
     L.chasm_options_default(C.byref(opt))
     opt.precision = precision
     opt.n_nb = n_nb
+    opt.theta_form = theta_form
     return L.chasm_workspace_bytes(C.byref(g), C.byref(pot), C.byref(opt))
 
 

@@ -76,8 +76,19 @@ std::string validate(const chasm_grid* grid, const chasm_box* box, const chasm_p
         return "options: patches[d] must divide nx[d] - 1";
       if (opt->patches[d] != 1) return "options: only patches = 1 is implemented";
     }
+    if (opt->theta_form != CHASM_THETA_AUTO && opt->theta_form != CHASM_THETA_TABLE &&
+        opt->theta_form != CHASM_THETA_MODULATED)
+      return "options: theta_form must be CHASM_THETA_AUTO, _TABLE or _MODULATED";
   }
   return std::string();
+}
+
+// Whether the Coulomb operator uses the per-x symbol table (CHASM_THETA_AUTO: table up to
+// kXsAutoMaxBytes).
+bool table_form(int nk, int64_t nxp, size_t elt, const chasm_options& o) {
+  if (o.theta_form == CHASM_THETA_TABLE) return true;
+  if (o.theta_form == CHASM_THETA_MODULATED) return false;
+  return xs_table_bytes(nk, nxp, elt) <= kXsAutoMaxBytes;
 }
 
 chasm_options defaults() {
@@ -87,6 +98,7 @@ chasm_options defaults() {
   o.patches[0] = o.patches[1] = o.patches[2] = 1;
   o.use_graphs = 1;
   o.cuda_stream = nullptr;
+  o.theta_form = CHASM_THETA_AUTO;
   return o;
 }
 
@@ -409,7 +421,7 @@ void free_all(Handle* H) {
   if (H->graph) cudaGraphExecDestroy(H->graph);
   H->graph = nullptr;
   void* ptrs[] = {H->d_clos[0], H->d_clos[1], H->d_clos[2], H->d_lu[0], H->d_lu[1], H->d_lu[2], H->adv.dev, H->d_T,
-                  H->d_that, H->d_phase, H->d_scratch, H->d_u[0], H->d_u[1], H->d_krows,
+                  H->d_that, H->d_phase, H->d_sig, H->d_scratch, H->d_u[0], H->d_u[1], H->d_krows,
                   H->d_partials, H->d_result, H->d_vx, H->d_fhost};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, H->stream);
@@ -439,6 +451,11 @@ int do_pflow(Handle* H, void* f, double dt) {
   if (H->nuclei.empty()) {
     if (H->kappa == 0.0) return CHASM_OK;
     for (int d = 0; d < 3; ++d) CHASM_CUDA(H, launch_kshift(*H, f, d, H->d_krows, H->stream));
+    return CHASM_OK;
+  }
+  if (H->xs) {   // the four stages per x point in one launch, in place on f
+    const double c[4] = {dt / 4, dt / 3, dt / 2, dt};
+    CHASM_CUDA(H, launch_theta_xs(*H, f, f, f, 4, c, H->stream));
     return CHASM_OK;
   }
   // u <- f + (dt/s) Theta[u], s = 4, 3, 2, 1, u_0 = f; buffers f -> u0 -> u1 -> u0 -> f
@@ -510,16 +527,22 @@ size_t chasm_workspace_bytes(const chasm_grid* grid, const chasm_potential* pot,
   size_t w = 0;
   const bool coulomb = pot && pot->n_nuc > 0;
   if (coulomb) {
-    w += 2 * fbytes;
+    const bool xs = table_form(nk, nxp, e, o);
     int dev = 0;
     cudaGetDevice(&dev);
     int sms = 152;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 152;
     ThetaPlan tp;
-    theta_plan(nk, fp64, nxp, sms, &tp);
+    if (xs) {
+      w += xs_table_bytes(nk, nxp, e);
+      theta_xs_plan(nk, fp64, nxp, sms, &tp);
+    } else {
+      w += 2 * fbytes;
+      theta_plan(nk, fp64, nxp, sms, &tp);
+      w += (size_t)pot->n_nuc * (grid->nx[0] + grid->nx[1] + 4 * grid->nx[2]) * nk * 2 * e;
+    }
     w += tp.scratch_bytes;
     w += (size_t)8 * nk * nk * nk * e + (size_t)(2 * nk - 1) * (2 * nk - 1) * (2 * nk - 1) * 8;
-    w += (size_t)pot->n_nuc * (grid->nx[0] + grid->nx[1] + 4 * grid->nx[2]) * nk * 2 * e;
   }
   w += (size_t)nxp * 8 + 3 * (size_t)moments_blocks() * 8 + 64;
   w += (size_t)3 * (grid->nx[0] + grid->nx[1] + grid->nx[2]) * (8 + 2 * e);
@@ -609,14 +632,26 @@ int chasm_create(const chasm_grid* grid, const chasm_box* box, const chasm_poten
       return bail(fail(H, CHASM_ENOMEM, "device allocation failed (symbol)"));
     e = compute_symbol(N, g.lk, H->d_T, H->d_that, H->fp64, &H->that_absmax, H->stream);
     if (e != cudaSuccess) return bail(cuda_fail(H, e, "symbol precompute"));
-    rc = build_phase_tables(H);
-    if (rc) return bail(rc);
-    theta_plan(N, H->fp64, g.nxp, H->num_sms, &H->theta);
-    const size_t sb = H->theta.scratch_bytes;
-    if ((sb > 0 && cudaMallocAsync(&H->d_scratch, sb, H->stream) != cudaSuccess) ||
-        cudaMallocAsync(&H->d_u[0], fbytes, H->stream) != cudaSuccess ||
-        cudaMallocAsync(&H->d_u[1], fbytes, H->stream) != cudaSuccess)
-      return bail(fail(H, CHASM_ENOMEM, "device allocation failed (Horner buffers / scratch)"));
+    H->xs = table_form(N, g.nxp, H->elt, o);
+    if (H->xs) {
+      if (cudaMallocAsync(&H->d_sig, xs_table_bytes(N, g.nxp, H->elt), H->stream) != cudaSuccess)
+        return bail(fail(H, CHASM_ENOMEM, "device allocation failed (per-x symbol table)"));
+      e = build_xs_table(*H, H->d_sig, H->stream);
+      if (e != cudaSuccess) return bail(cuda_fail(H, e, "per-x symbol table"));
+      theta_xs_plan(N, H->fp64, g.nxp, H->num_sms, &H->theta);
+      const size_t sb = H->theta.scratch_bytes;
+      if (sb > 0 && cudaMallocAsync(&H->d_scratch, sb, H->stream) != cudaSuccess)
+        return bail(fail(H, CHASM_ENOMEM, "device allocation failed (Theta scratch)"));
+    } else {
+      rc = build_phase_tables(H);
+      if (rc) return bail(rc);
+      theta_plan(N, H->fp64, g.nxp, H->num_sms, &H->theta);
+      const size_t sb = H->theta.scratch_bytes;
+      if ((sb > 0 && cudaMallocAsync(&H->d_scratch, sb, H->stream) != cudaSuccess) ||
+          cudaMallocAsync(&H->d_u[0], fbytes, H->stream) != cudaSuccess ||
+          cudaMallocAsync(&H->d_u[1], fbytes, H->stream) != cudaSuccess)
+        return bail(fail(H, CHASM_ENOMEM, "device allocation failed (Horner buffers / scratch)"));
+    }
   }
   e = cudaStreamSynchronize(H->stream);
   if (e != cudaSuccess) return bail(cuda_fail(H, e, "create"));
@@ -737,6 +772,11 @@ int chasm_theta(chasm_handle* h, const void* u, void* out) {
   if (u == out) return fail(H, CHASM_EINVAL, "u and out must not alias");
   if (((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(out)) & 15) != 0)
     return fail(H, CHASM_EINVAL, "u/out must be 16-byte aligned");
+  if (H->xs) {
+    const double one = 1.0;
+    CHASM_CUDA(H, launch_theta_xs(*H, u, nullptr, out, 1, &one, H->stream));
+    return CHASM_OK;
+  }
   double coef[kMaxNuclei];
   for (size_t a = 0; a < H->nuclei.size(); ++a)
     coef[a] = -(2.0 * H->nuclei[a].charge / (M_PI * M_PI * H->hbar));

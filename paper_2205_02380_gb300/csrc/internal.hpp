@@ -54,6 +54,15 @@ struct ThetaPlan {
   size_t scratch_bytes = 0; // global scratch of the fallback kernel
 };
 void theta_plan(int nk, bool fp64, int64_t nxp, int num_sms, ThetaPlan* plan);
+// real form with the per-x symbol table (k_theta_xs.cu): u_0 = in, u_{s+1} = (base or 0) +
+// coef[s] Theta^T[u_s] for s < nst (1..4), out = u_nst; out may alias in and base
+cudaError_t launch_theta_xs(const Handle& H, const void* in, const void* base, void* out, int nst,
+                            const double* coef, cudaStream_t s);
+void theta_xs_plan(int nk, bool fp64, int64_t nxp, int num_sms, ThetaPlan* plan);
+// the per-x symbol table (k_xsym.cu), [nxp][N][2N][2N] in the storage type; needs H.d_T
+size_t xs_table_bytes(int nk, int64_t nxp, size_t elt);
+cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s);
+constexpr size_t kXsAutoMaxBytes = (size_t)64 << 30;   // CHASM_THETA_AUTO: table form up to 64 GiB
 // symbol precompute (k_symbol.cu): T (FP64, (2N-1)^3) and T-hat (parity-major, scaled)
 cudaError_t compute_symbol(int nk, double lk, double* T_dev, void* that_dev, bool fp64,
                            double* that_absmax_host, cudaStream_t s);
@@ -97,6 +106,8 @@ struct Handle {
   void* d_that = nullptr;          // T-hat, storage type, (2N)^3 parity-major, / (2N)^3
   double that_absmax = 0.0;
   void* d_phase = nullptr;         // modulation tables (storage type complex)
+  bool xs = false;                 // table (real) form of Theta^T, else the modulated form
+  void* d_sig = nullptr;           // per-x symbol table of the table form
   ThetaPlan theta;                 // launch plan of the Theta kernel
   void* d_scratch = nullptr;       // per-CTA scratch of the global-scratch Theta kernel
   void* d_u[2] = {nullptr, nullptr};  // Horner buffers

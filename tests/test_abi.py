@@ -45,18 +45,19 @@ def test_struct_layouts_match_the_header(ch):
     assert C.sizeof(ch.Box) == 72
     assert C.sizeof(ch.Nucleus) == 32
     assert C.sizeof(ch.Gaussian) == 72
-    assert C.sizeof(ch.Options) == 32
+    assert C.sizeof(ch.Options) == 40
 
 
 def test_options_default(ch):
     o = ch.Options()
     assert ch.lib().chasm_options_default(C.byref(o)) == 0
     assert (o.precision, o.n_nb, list(o.patches), o.use_graphs) == (ch.FP32_MIXED, 20, [1, 1, 1], 1)
+    assert o.theta_form == ch.THETA_AUTO
     assert ch.lib().chasm_options_default(None) == ch.EINVAL
 
 
 def _create(ch, nx=(8, 8, 8), nk=16, lo=-4.0, hi=4.0, lk=4.0, nuclei=(), hbar=1.0, m=1.0,
-            precision=0, n_nb=20, patches=(1, 1, 1)):
+            precision=0, n_nb=20, patches=(1, 1, 1), theta_form=0):
     L = ch.lib()
     g = ch.make_grid(list(nx), nk) if not isinstance(nk, tuple) else ch.Grid(
         (C.c_int32 * 3)(*nx), (C.c_int32 * 3)(*nk))
@@ -68,6 +69,7 @@ def _create(ch, nx=(8, 8, 8), nk=16, lo=-4.0, hi=4.0, lk=4.0, nuclei=(), hbar=1.
     o.precision = precision
     o.n_nb = n_nb
     o.patches = (C.c_int32 * 3)(*patches)
+    o.theta_form = theta_form
     h = C.c_void_p()
     rc = L.chasm_create(C.byref(g), C.byref(b), C.byref(pot), hbar, m, C.byref(o), C.byref(h))
     return rc, L.chasm_last_error(None).decode()
@@ -86,6 +88,7 @@ def _create(ch, nx=(8, 8, 8), nk=16, lo=-4.0, hi=4.0, lk=4.0, nuclei=(), hbar=1.
     (dict(patches=(2, 1, 1), nx=(8, 8, 8)), "divide"),
     (dict(patches=(7, 1, 1), nx=(8, 8, 8)), "patches"),
     (dict(nuclei=[((float("nan"), 0, 0), 1.0)]), "nucleus"),
+    (dict(theta_form=3), "theta_form"),
 ])
 def test_create_rejects_invalid_arguments_on_the_host(ch, kw, needle):
     rc, msg = _create(ch, **kw)
@@ -101,6 +104,24 @@ def test_workspace_bytes(ch):
     assert 0 < w32 < 16 ** 6 * 4 // 10        # the harmonic form needs only small tables
     bad = ch.make_grid([16, 16, 16], 12)
     assert L.chasm_workspace_bytes(C.byref(bad), C.byref(pot), None) == 0
+
+
+def test_workspace_bytes_of_the_two_theta_forms(ch):
+    """Coulomb workspace: the table form holds 4 N_k^3 values per x point (four copies of f) and
+    no Horner buffers; the modulated form two Horner buffers; AUTO picks the table when it needs
+    at most 64 GiB."""
+    nuc = [((0.0, 0.0, 0.0), 1.0)]
+    f = 16 ** 6 * 4
+    w_tab = ch.workspace_bytes(16, 16, nuclei=nuc, theta_form=ch.THETA_TABLE)
+    w_mod = ch.workspace_bytes(16, 16, nuclei=nuc, theta_form=ch.THETA_MODULATED)
+    w_auto = ch.workspace_bytes(16, 16, nuclei=nuc)
+    assert 4 * f <= w_tab < 5 * f
+    assert 2 * f <= w_mod < 4 * f
+    assert w_auto == w_tab
+    # 64^3 x 32^3 FP32: a 137 GB table is above the AUTO limit
+    big_tab = ch.workspace_bytes(64, 32, nuclei=nuc, theta_form=ch.THETA_TABLE)
+    assert big_tab >= 4 * 64 ** 3 * 32 ** 3 * 4
+    assert ch.workspace_bytes(64, 32, nuclei=nuc) < big_tab
 
 
 def test_null_handles_are_rejected(ch):

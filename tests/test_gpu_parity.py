@@ -19,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
+FORMS = ["table", "modulated"]
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +54,12 @@ def problem(nx, nk, lo, hi, lk, **kw):
     return O.Problem(nx=nx, nk=nk, x_lo=lo, x_hi=hi, lk=lk, **kw)
 
 
-def solver(ch, prob, name, **kw):
+def theta_form(ch, form):
+    return {"table": ch.THETA_TABLE, "modulated": ch.THETA_MODULATED, "auto": ch.THETA_AUTO}[form]
+
+
+def solver(ch, prob, name, form="auto", **kw):
+    kw.setdefault("theta_form", theta_form(ch, form))
     return ch.Solver(prob.nx, prob.nk, prob.x_lo, prob.x_hi, prob.lk, nuclei=prob.nuclei,
                      kappa=prob.kappa, center=prob.center, hbar=prob.hbar, m=prob.m,
                      precision=prec(ch, name), n_nb=prob.n_nb, **kw)
@@ -78,13 +84,14 @@ def test_symbol_tensor_matches_oracle(ch, nk):
     assert np.max(np.abs(out - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("name", ["fp64", "fp32"])
 @pytest.mark.parametrize("nk,nx", [(8, (5, 4, 6)), (16, (4, 5, 4)), (32, (4, 4, 5))])
-def test_theta_matches_oracle(ch, name, nk, nx):
+def test_theta_matches_oracle(ch, name, nk, nx, form):
     prob = problem(nx, nk, (-2.0, -1.5, -2.5), (2.5, 1.0, 2.0), 4.0,
                    nuclei=[((0.3, -0.2, 0.1), 1.0), ((-0.4, 0.25, -0.3), 0.7)])
     f0 = rough_input(prob, 11)
-    with solver(ch, prob, name) as s:
+    with solver(ch, prob, name, form) as s:
         u = to_dev(f0, name)
         out = torch.empty_like(u)
         s.theta(u, out)
@@ -120,12 +127,13 @@ def test_advect_truncated_stencils_match_oracle(ch, n_nb):
     assert O.rel_l2(got, O.advect(f0, prob, 0.3)) <= 1e-12
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("name", ["fp64", "fp32"])
-def test_pflow_coulomb_matches_oracle(ch, name):
+def test_pflow_coulomb_matches_oracle(ch, name, form):
     prob = problem((4, 5, 4), 16, (-2.0, -1.5, -2.0), (2.0, 1.5, 2.5), 4.0,
                    nuclei=[((0.1, 0.2, -0.1), 1.0)])
     f0 = rough_input(prob, 3)
-    with solver(ch, prob, name) as s:
+    with solver(ch, prob, name, form) as s:
         f = to_dev(f0, name)
         s.pflow(f, 0.05)
         s.sync()
@@ -149,8 +157,9 @@ def test_pflow_harmonic_matches_oracle(ch, name, nk):
 
 
 @pytest.mark.parametrize("name", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["coulomb1", "coulomb2", "harmonic"])
+@pytest.mark.parametrize("case", ["coulomb1", "coulomb2", "coulomb2-modulated", "harmonic"])
 def test_strang_steps_match_oracle(ch, name, case):
+    form = "modulated" if case.endswith("modulated") else "table"
     if case == "harmonic":
         prob = problem((9, 8, 7), 8, -4.0, 4.0, 4.0, kappa=1.0)
         nsteps, dt = 3, 0.05
@@ -161,7 +170,7 @@ def test_strang_steps_match_oracle(ch, name, case):
         nsteps, dt = 2, 0.025
     pk = [synth.packet((0.5, -0.2, 0.1), (0.3, 0.0, -0.2))]
     f0 = synth.gaussian_packets(prob.nx, prob.nk, prob.x_lo, prob.x_hi, prob.lk, pk)
-    with solver(ch, prob, name) as s:
+    with solver(ch, prob, name, "auto" if case == "harmonic" else form) as s:
         f = to_dev(f0, name)
         s.step(f, dt, nsteps)
         s.sync()
@@ -246,14 +255,14 @@ def test_errors_are_reported_not_raised_on_device(ch):
 @pytest.mark.parametrize("name,nk,nx", [("fp32", 32, (4, 5, 4)), ("fp32", 16, (6, 5, 4)),
                                         ("fp64", 16, (4, 5, 6)), ("fp32", 8, (7, 5, 6))])
 def test_theta_kernel_variants_match_oracle(ch, monkeypatch, variant, name, nk, nx):
-    """Both implementations of the Theta kernel (per-CTA global scratch, and the spectrum held in
-    the shared memory of one CTA or of a thread-block cluster) against the oracle, with two
-    nuclei so the per-nucleus accumulation is exercised."""
+    """Both implementations of the modulated-form Theta kernel (per-CTA global scratch, and the
+    spectrum held in the shared memory of one CTA or of a thread-block cluster) against the
+    oracle, with two nuclei so the per-nucleus accumulation is exercised."""
     monkeypatch.setenv("CHASM_THETA_VARIANT", variant)
     prob = problem(nx, nk, (-2.0, -1.5, -2.5), (2.5, 1.0, 2.0), 4.0,
                    nuclei=[((0.3, -0.2, 0.1), 1.0), ((-0.4, 0.25, -0.3), 0.7)])
     f0 = rough_input(prob, 13)
-    with solver(ch, prob, name) as s:
+    with solver(ch, prob, name, "modulated") as s:
         u = to_dev(f0, name)
         out = torch.empty_like(u)
         s.theta(u, out)
@@ -266,3 +275,42 @@ def test_theta_kernel_variants_match_oracle(ch, monkeypatch, variant, name, nk, 
     assert O.rel_l2(got, ref) <= TOL[name], O.rel_l2(got, ref)
     ref_p = O.pflow_coulomb(oracle_input(f0 * 0.5, name), prob, 0.02)
     assert O.rel_l2(got_p, ref_p) <= TOL[name], O.rel_l2(got_p, ref_p)
+
+
+@pytest.mark.parametrize("name,nk,nx", [("fp32", 32, (5, 7, 9)), ("fp64", 32, (4, 4, 5)),
+                                        ("fp32", 16, (11, 9, 7)), ("fp64", 8, (9, 8, 7))])
+def test_table_form_many_points_three_nuclei(ch, name, nk, nx):
+    """Table form with more x points than one wave of CTAs covers (ragged last wave), three
+    nuclei folded into one symbol, Theta out of place and P(dt) in place."""
+    prob = problem(nx, nk, (-3.0, -2.5, -3.5), (3.5, 2.0, 3.0), 4.0,
+                   nuclei=[((0.3, -0.2, 0.1), 1.0), ((-0.4, 0.25, -0.3), 0.7),
+                           ((1.1, 0.6, -0.9), 2.0)])
+    f0 = rough_input(prob, 17)
+    with solver(ch, prob, name, "table") as s:
+        u = to_dev(f0, name)
+        out = torch.empty_like(u)
+        s.theta(u, out)
+        s.pflow(u, 0.01)
+        s.sync()
+        got = out.double().cpu().numpy()
+        got_p = u.double().cpu().numpy()
+    fo = oracle_input(f0, name)
+    ref = O.theta_coulomb(fo, prob)
+    assert O.rel_l2(got, ref) <= TOL[name], O.rel_l2(got, ref)
+    ref_p = O.pflow_coulomb(fo, prob, 0.01)
+    assert O.rel_l2(got_p, ref_p) <= TOL[name], O.rel_l2(got_p, ref_p)
+
+
+def test_table_and_modulated_forms_agree(ch):
+    """The two evaluations of the same operator on the same FP64 input agree to rounding."""
+    prob = problem((6, 5, 7), 16, -3.0, 3.0, 4.0, nuclei=[((0.2, -0.1, 0.3), 1.0),
+                                                          ((-0.6, 0.4, 0.0), 1.0)])
+    f0 = rough_input(prob, 23)
+    outs = []
+    for form in FORMS:
+        with solver(ch, prob, "fp64", form) as s:
+            f = to_dev(f0, "fp64")
+            s.step(f, 0.02, 2)
+            s.sync()
+            outs.append(f.cpu().numpy())
+    assert O.rel_l2(outs[0], outs[1]) <= 1e-13
