@@ -38,14 +38,23 @@ WORKLOAD = {
 
 
 # ------------------------------------------------------------------------------------------------
-# algorithmic work of the dominant kernel (the Theta kernel, one launch = one Horner stage)
+# algorithmic work of the dominant kernel (the P(dt) kernel of the table form: one launch = the
+# four Horner stages of P(dt) over all x points; each stage applies Theta^T once)
 def theta_flops_per_cell(nk: int) -> float:
-    """Per cell and nucleus: 14 N^2 padded length-2N complex FFTs at 5 L log2 L flops
-    (L = 2N), the symbol multiply 2 (2N)^3, modulation 2 N^3 and demodulation/Im/scale 4 N^3,
-    all divided by N^3."""
-    L = 2 * nk
-    fft = 14 * nk * nk * 5 * L * math.log2(L)
-    return (fft + 2 * L ** 3 + 6 * nk ** 3) / nk ** 3
+    """Flops per cell of one application of Theta^T in the table form (all nuclei at once),
+    complex FFTs of length n counted at 5 n log2 n:
+      k3 forward   N^2 FFTs of length N on the twisted real line (twist 2 N^3)
+      slab phase   6 N^2 zero-padded length-2N transforms (k2 and k1 forward, k1 and k2 inverse),
+                   each two N-point FFTs plus the twist of the odd half (6 N), and the parity-
+                   half sum of the 3 N^2 inverse ones (2 N each)
+      symbol       (2N)^2 N products by i sigma (2 each)
+      k3 inverse   N^2 FFTs of length N, conjugate twist and real part (3 N^3), Horner (2 N^3)
+    all divided by N^3 (about 407 at N = 32)."""
+    n = nk
+    fft_n = 5 * n * math.log2(n)
+    total = (2 * n * n * fft_n + 6 * n * n * (2 * fft_n + 6 * n) + 3 * n * n * 2 * n
+             + 8 * n ** 3 + (2 + 3 + 2) * n ** 3)
+    return total / n ** 3
 
 
 def fp32_alu_peak_tflops() -> float:
@@ -59,8 +68,11 @@ def fp32_alu_peak_tflops() -> float:
 
 
 def theta_source_hash() -> str:
-    p = os.path.join(ROOT, "paper_2205_02380_gb300", "csrc", "k_theta.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Hash of the sources of the P(dt) kernel (the traffic figure is void once they change)."""
+    h = hashlib.sha256()
+    for name in ("k_theta_xs.cu", "fft_reg.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2205_02380_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def committed_traffic():
@@ -71,7 +83,7 @@ def committed_traffic():
         d = json.load(open(p))
     except Exception:
         return None
-    if d.get("k_theta_sha256_16") != theta_source_hash():
+    if d.get("source_sha256_16") != theta_source_hash():
         return None
     return d
 
@@ -135,7 +147,7 @@ class ClockSampler:
 def make_solver(ch, precision, stream):
     W = WORKLOAD
     return ch.Solver(W["nx"], W["nk"], -W["L"], W["L"], W["lk"], nuclei=W["nuclei"],
-                     precision=precision, stream=stream.cuda_stream)
+                     precision=precision, stream=stream.cuda_stream, theta_form=ch.THETA_TABLE)
 
 
 def aggregate_ranks(ms_local: float, cells: int, steps: int, dist=None, device="cpu"):
@@ -172,19 +184,20 @@ def time_steps(torch, s, f, dt, steps, warmup, stream, dist):
     return e0.elapsed_time(e1)
 
 
-def time_theta_launches(torch, s, f, stream, reps):
-    """Average duration of one launch of the Theta kernel (chasm_theta = exactly one launch)."""
-    out = torch.empty_like(f)
-    s.theta(f, out)
+def time_pflow_launches(torch, s, f, dt, stream, reps):
+    """Average duration of one launch of the P(dt) kernel (in the table form chasm_pflow is
+    exactly one launch), on a copy of f, CUDA events on the solver's stream."""
+    g = f.clone()
+    s.pflow(g, dt)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        s.theta(f, out)
+        s.pflow(g, dt)
     e1.record(stream)
     torch.cuda.synchronize()
-    del out
+    del g
     return e0.elapsed_time(e1) / reps
 
 
@@ -317,7 +330,7 @@ def run_chasm(args):
                      "mass0": m0, "mass": m1, "energy0": e0, "energy": e1}
             if prec_name == "fp32":
                 reps = 5
-                entry["theta_ms"] = time_theta_launches(torch, s, f, stream, reps)
+                entry["pflow_ms"] = time_pflow_launches(torch, s, f, dt, stream, reps)
                 # end-to-end through the C ABI with HOST buffers (pinned), copies included
                 host = torch.empty(f.shape, dtype=dtp, pin_memory=True)
                 host.copy_(f.cpu())
@@ -353,8 +366,8 @@ def run_chasm(args):
         return
     r32, r64 = result["fp32"], result["fp64"]
     nk = W["nk"]
-    flops_launch = theta_flops_per_cell(nk) * cells * len(W["nuclei"])
-    achieved = flops_launch / (r32["theta_ms"] / 1e3) / 1e12
+    flops_launch = 4 * theta_flops_per_cell(nk) * cells
+    achieved = flops_launch / (r32["pflow_ms"] / 1e3) / 1e12
     peak = fp32_alu_peak_tflops()
     tr = committed_traffic()
     line = {
@@ -369,14 +382,16 @@ def run_chasm(args):
                  "dtype": "f64"},
         "accuracy": accuracy,
         "serving": serving,
-        "roofline": {"kernel": "k_theta (one Horner stage of P: Theta^T over all x points)",
+        "roofline": {"kernel": "k_theta_xs (P(dt): four Horner stages of Theta^T per x point, "
+                               "table form)",
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                     "ms_per_launch": r32["theta_ms"],
+                     "ms_per_launch": r32["pflow_ms"],
+                     "flops_per_launch": flops_launch,
                      "traffic": (tr["dram_bytes_per_launch"] * cells / tr["cells"]) if tr else None},
         "e2e": r32["e2e"],
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "clocks": clocks,
         "cpu_baseline": base,
     }

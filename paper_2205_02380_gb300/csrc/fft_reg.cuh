@@ -245,6 +245,24 @@ __device__ __forceinline__ void st_keep(cpx<double>* p, cpx<double> v, uint64_t 
                "l"(pol)
                : "memory");
 }
+// streamed read-only data (the per-x symbol table) with an L2 evict-first policy, so that it does
+// not displace the spectrum scratch
+__device__ __forceinline__ uint64_t l2_stream_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 // two adjacent single-precision complex values per access (16-byte aligned)
 __device__ __forceinline__ void ld2_keep(const cpx<float>* p, uint64_t pol, cpx<float>& a, cpx<float>& b) {
   asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
@@ -380,9 +398,11 @@ __device__ __forceinline__ void slab_conv(cpx<T>* Gs, cpx<T>* V, const T* __rest
     if (h) twist<T, N, false>(re, im);
     fft<T, N, false>(re, im);
     const T* t = th + (size_t)(h * N) * L + c;
+    uint64_t spol = 0;
+    if constexpr (IMAG) spol = l2_stream_policy();
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      const T w = __ldg(t + (size_t)j * L);
+      const T w = IMAG ? ld_stream(t + (size_t)j * L, spol) : __ldg(t + (size_t)j * L);
       if constexpr (IMAG) {
         const T a = re[j];
         re[j] = -w * im[j];

@@ -168,6 +168,11 @@ __device__ __forceinline__ void load_line_plain(const T* src, T (&v)[N]) {
   }
 }
 
+// bytes (a multiple of 16, 16-byte aligned source) towards L2, asynchronously, no completion
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 template <typename T, int N, int NT, bool GSM, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
   using C = XsCfg<T, N>;
@@ -182,16 +187,11 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
   const uint64_t pol = l2_keep_policy();
 
   for (int64_t xp = blockIdx.x; xp < p.nxp; xp += gridDim.x) {
-    const T* __restrict__ sig = p.sig + xp * (int64_t)(N * L * L);
-    const T* u = p.in + xp * N3;
-    const T* b = p.base ? p.base + xp * N3 : nullptr;
-    T* o = p.out + xp * N3;
-
     // ---- Phase A: twist + FFT along k3 of the stage-0 input ----
     for (int line = tid; line < N2; line += NT) {
       const int off = (line / N) * SR + (line % N);
       T re[N], im[N];
-      load_line_plain<T, N>(u + (size_t)line * N, re);
+      load_line_plain<T, N>(p.in + xp * N3 + (size_t)line * N, re);
       twist_real<T, N>(re, im);
       fft<T, N, false>(re, im);
       store_col<T, N, GSM>(G + off, SLAB, re, im, pol);
@@ -200,8 +200,15 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
 
     for (int st = 0; st < p.nst; ++st) {
       // ---- Phase B: per slab j, the 2-D padded convolution with i sigma_j ----
-      for (int s = grp; s < N; s += NG)
-        slab_conv<T, N, GS, SR, !GSM, true>(G + (size_t)s * SLAB, V, sig + (size_t)s * L * L, tg, grp, pol);
+      for (int s = grp; s < N; s += NG) {
+        if (tg == 0) {   // the symbol slab this group needs next, into L2 (one bulk prefetch)
+          const int sn = s + NG < N ? s + NG : grp;
+          const int64_t xn = s + NG < N || st + 1 < p.nst ? xp : xp + gridDim.x;
+          if (xn < p.nxp) bulk_prefetch_l2(p.sig + (xn * N + sn) * (int64_t)(L * L), L * L * sizeof(T));
+        }
+        slab_conv<T, N, GS, SR, !GSM, true>(G + (size_t)s * SLAB, V,
+                                            p.sig + (xp * N + s) * (int64_t)(L * L), tg, grp, pol);
+      }
       __syncthreads();
 
       T c = p.coef[0];   // static indexing keeps the parameter block out of local memory
@@ -216,9 +223,9 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
         T re[N], im[N];
         load_col<T, N, GSM>(G + off, SLAB, re, im, pol);
         fft<T, N, true>(re, im);
-        horner_line<T, N>(re, im, b ? b + (size_t)line * N : nullptr, c);
+        horner_line<T, N>(re, im, p.base ? p.base + xp * N3 + (size_t)line * N : nullptr, c);
         if (last) {
-          store_line_cs<T, N>(o + (size_t)line * N, re);
+          store_line_cs<T, N>(p.out + xp * N3 + (size_t)line * N, re);
         } else {
           twist_real<T, N>(re, im);
           fft<T, N, false>(re, im);
