@@ -186,6 +186,11 @@ int build_spline_plan(Handle* H) {
       cm[j] = (-rows[2][N - j + 1] + rows[3][N - j + 1]) / (2.0 * h);
     }
     H->J[d] = J;
+    H->h_clos[d].assign(2 * (size_t)n, 0.0);
+    for (int j = 0; j < J; ++j) {
+      H->h_clos[d][j] = cp[j];
+      H->h_clos[d][n + j] = cm[j];
+    }
     int rc;
     if (H->fp64) {
       std::vector<double> c(2 * (size_t)n, 0.0);
@@ -223,6 +228,7 @@ int build_spline_plan(Handle* H) {
     }
     rc = upload_real(H, &H->d_lu[d], lu);
     if (rc) return rc;
+    H->h_lu[d] = lu;
   }
   return CHASM_OK;
 }

@@ -99,6 +99,9 @@ struct Handle {
   // [c+ hi | c+ lo | c- hi | c- lo] (unevaluated float pairs for the compensated dot product)
   void* d_clos[3] = {nullptr, nullptr, nullptr};
   void* d_lu[3] = {nullptr, nullptr, nullptr};   // [cprime (n) | mult (n)] in storage type
+  // host copies (FP64) of the closure stencils [c+ (n) | c- (n)] and LU factors [cprime | mult],
+  // passed by value to the register advection kernel
+  std::vector<double> h_clos[3], h_lu[3];
 
   AdvectTables adv;                // current tau tables
   // Coulomb

@@ -23,6 +23,8 @@
 // from {16, 24, 32, 48, 64} and integer shift in [-2, 1], the usual case since |alpha| < 1);
 // k_advect_smem is the general fallback with the line in shared memory (column layout, element
 // e of thread t at e*B + t, conflict-free).
+#include <cstring>
+
 #include "internal.hpp"
 
 namespace chasm {
@@ -104,6 +106,36 @@ struct Closure<float> {
   }
 };
 
+// Closure stencils and Thomas factors of the register kernel, passed by value in the kernel's
+// parameter block: every index is a compile-time constant there, so each coefficient is a
+// constant-bank operand of its FMA instead of a load per line.
+constexpr int kRegMaxNx = 64;
+template <typename T>
+struct AdvTabs;
+template <>
+struct AdvTabs<float> {
+  float c[4][kRegMaxNx];     // c+ hi, c+ lo, c- hi, c- lo (zero-padded)
+  float lu[2][kRegMaxNx];    // c'_i, 1 / pivot_i
+};
+template <>
+struct AdvTabs<double> {
+  double c[2][kRegMaxNx];    // c+, c-
+  double lu[2][kRegMaxNx];
+};
+
+template <int NX>
+__device__ __forceinline__ void closure_tab(Closure<float>& cl, const AdvTabs<float>& tb, int j,
+                                            float phiL, float phiR) {
+  df_acc(cl.L, phiL, tb.c[0][j], tb.c[1][j]);
+  df_acc(cl.R, phiR, tb.c[2][j], tb.c[3][j]);
+}
+template <int NX>
+__device__ __forceinline__ void closure_tab(Closure<double>& cl, const AdvTabs<double>& tb, int j,
+                                            double phiL, double phiR) {
+  cl.L = fma(tb.c[0][j], phiL, cl.L);
+  cl.R = fma(tb.c[1][j], phiR, cl.R);
+}
+
 // the h arguments of the closure terms in the storage precision
 template <typename T>
 __device__ __forceinline__ T hval(const AdvParams<T>& p);
@@ -144,26 +176,27 @@ __device__ __forceinline__ void eval_store(const T (&v)[NX + 2], T w0, T w1, T w
   }
 }
 
-// One line in registers: closure, Thomas sweep, ghosts, 4-tap evaluation and store.
-template <typename T, int NX>
-__device__ __forceinline__ void solve_eval_line(const AdvParams<T>& p, T (&v)[NX + 2], int kd, T* dst,
-                                                int64_t s_d) {
+// One line in registers: closure, Thomas sweep, ghosts, 4-tap evaluation and store.  JC: the
+// number of closure taps evaluated (the stencil is zero beyond the launch's J <= JC).
+template <typename T, int NX, int JC>
+__device__ __forceinline__ void solve_eval_line(const AdvParams<T>& p, const AdvTabs<T>& tb,
+                                                T (&v)[NX + 2], int kd, T* dst, int64_t s_d) {
   constexpr int N = NX - 1;
   Closure<T> cl;
 #pragma unroll
-  for (int j = 0; j < NX; ++j) cl.add(p.clos, NX, j, v[j + 1], v[N - j + 1]);
+  for (int j = 0; j < JC; ++j) closure_tab<NX>(cl, tb, j, v[j + 1], v[N - j + 1]);
 
-  T dp = (T)cl.d0(v[1], hval(p)) * __ldg(p.mult);
+  T dp = (T)cl.d0(v[1], hval(p)) * tb.lu[1][0];
   v[1] = dp;
 #pragma unroll
   for (int i = 1; i < N; ++i) {
-    dp = ((T)6 * v[i + 1] - dp) * __ldg(p.mult + i);
+    dp = ((T)6 * v[i + 1] - dp) * tb.lu[1][i];
     v[i + 1] = dp;
   }
-  dp = ((T)cl.dN(v[N + 1], hval(p)) - dp) * __ldg(p.mult + N);
+  dp = ((T)cl.dN(v[N + 1], hval(p)) - dp) * tb.lu[1][N];
   v[N + 1] = dp;
 #pragma unroll
-  for (int i = N - 1; i >= 0; --i) v[i + 1] = v[i + 1] - __ldg(p.cprime + i) * v[i + 2];
+  for (int i = N - 1; i >= 0; --i) v[i + 1] = v[i + 1] - tb.lu[0][i] * v[i + 2];
   v[0] = (T)cl.gl(v[2], h2val(p));
   v[N + 2] = (T)cl.gr(v[N], h2val(p));
 
@@ -181,8 +214,8 @@ __device__ __forceinline__ void solve_eval_line(const AdvParams<T>& p, T (&v)[NX
 // FP64 form: one line per thread.  FP32-mixed form: two adjacent k (lines l and l + 1 share the
 // x indices) per thread, loaded with 8-byte accesses so each thread keeps twice the bytes in
 // flight.
-template <typename T, int NX>
-__global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p) {
+template <typename T, int NX, int JC>
+__global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p, const AdvTabs<T> tb) {
   constexpr int LPT = sizeof(T) == 4 ? 2 : 1;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t * LPT >= p.n_lines) return;
@@ -193,7 +226,7 @@ __global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p) {
     T v[NX + 2];   // slot nu + 1 holds eta_nu (phi_j before the solve)
 #pragma unroll
     for (int j = 0; j < NX; ++j) v[j + 1] = src[(int64_t)j * p.s_d];
-    solve_eval_line<T, NX>(p, v, kd, src, p.s_d);
+    solve_eval_line<T, NX, JC>(p, tb, v, kd, src, p.s_d);
   } else {
     T v0[NX + 2], v1[NX + 2];
 #pragma unroll
@@ -205,8 +238,8 @@ __global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p) {
     int kd1;
     T* src1;
     line_setup(p, t * LPT + 1, src1, kd1);
-    solve_eval_line<T, NX>(p, v0, kd, src, p.s_d);
-    solve_eval_line<T, NX>(p, v1, kd1, src1, p.s_d);
+    solve_eval_line<T, NX, JC>(p, tb, v0, kd, src, p.s_d);
+    solve_eval_line<T, NX, JC>(p, tb, v1, kd1, src1, p.s_d);
   }
 }
 
@@ -289,17 +322,44 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
   const int B = kAdvectThreads;
   const unsigned blocks = (unsigned)((p.n_lines + B - 1) / B);
   const bool reg_shift = H.adv.ns_min[dim] >= -2 && H.adv.ns_max[dim] <= 1;
-  if (reg_shift) {
+  if (reg_shift && p.n <= kRegMaxNx) {
     const int64_t lpt = sizeof(T) == 4 ? 2 : 1;   // kvol = nk^3 is even
     const unsigned rblocks = (unsigned)((p.n_lines / lpt + B - 1) / B);
+    AdvTabs<T> tb;
+    std::memset(&tb, 0, sizeof(tb));
+    const std::vector<double>& hc = H.h_clos[dim];
+    const std::vector<double>& hl = H.h_lu[dim];
+    for (int j = 0; j < p.n; ++j) {
+      if constexpr (sizeof(T) == 4) {   // unevaluated float pairs hi + lo of the FP64 stencils
+        tb.c[0][j] = (float)hc[j];
+        tb.c[1][j] = (float)(hc[j] - (double)tb.c[0][j]);
+        tb.c[2][j] = (float)hc[p.n + j];
+        tb.c[3][j] = (float)(hc[p.n + j] - (double)tb.c[2][j]);
+      } else {
+        tb.c[0][j] = hc[j];
+        tb.c[1][j] = hc[p.n + j];
+      }
+      tb.lu[0][j] = (T)hl[j];
+      tb.lu[1][j] = (T)hl[p.n + j];
+    }
+    // closure taps: the launch's J rounded up to a compiled bucket (the stencil is zero beyond J)
+    const bool short_j = p.J <= 24 && p.n > 24;
+#define CHASM_REG(NX)                                                                   \
+  case NX:                                                                              \
+    if (short_j && NX > 24)                                                             \
+      k_advect_reg<T, NX, (NX > 24 ? 24 : NX)><<<rblocks, B, 0, s>>>(p, tb);            \
+    else                                                                                \
+      k_advect_reg<T, NX, NX><<<rblocks, B, 0, s>>>(p, tb);                             \
+    return cudaGetLastError();
     switch (p.n) {
-      case 16: k_advect_reg<T, 16><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
-      case 24: k_advect_reg<T, 24><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
-      case 32: k_advect_reg<T, 32><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
-      case 48: k_advect_reg<T, 48><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
-      case 64: k_advect_reg<T, 64><<<rblocks, B, 0, s>>>(p); return cudaGetLastError();
+      CHASM_REG(16)
+      CHASM_REG(24)
+      CHASM_REG(32)
+      CHASM_REG(48)
+      CHASM_REG(64)
       default: break;
     }
+#undef CHASM_REG
   }
   const size_t smem = (size_t)(g.nx[dim] + 2) * B * sizeof(T);
   k_advect_smem<T><<<blocks, B, smem, s>>>(p);
