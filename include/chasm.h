@@ -67,6 +67,19 @@ enum { CHASM_FP32_MIXED = 0, CHASM_FP64 = 1 };
  *     modulated form. */
 enum { CHASM_THETA_AUTO = 0, CHASM_THETA_TABLE = 1, CHASM_THETA_MODULATED = 2 };
 
+/* Time integrator of chasm_step (chasm_options.integrator).
+ *   CHASM_STRANG (default): S(dt) = A(dt/2) P(dt) A(dt/2), P the Horner-Taylor-4 flow of Theta^T
+ *     (Coulomb) or the exact k-shift (quadratic potential).
+ *   CHASM_LPC1: the one-stage Lawson predictor-corrector of Sec. 2.2,
+ *       f~  = f(A_dt) + dt Theta_V[f](A_dt),
+ *       f'  = f(A_dt) + dt/2 Theta_V[f~] + dt/2 Theta_V[f](A_dt),
+ *     g(A_dt(x, k)) = g(x - hbar k dt / m, k) evaluated by the advection of Sec. 3 (one
+ *     advection of f and one of Theta_V[f] per step) and Theta_V applied twice per step; for the
+ *     quadratic potential Theta_V f = kappa (x - c)/hbar . grad_k f with the spectral k-derivative.
+ *     Needs two more copies of f of workspace (the modulated Coulomb form already has them).
+ *     EUNSTABLE when dt rho > 1, rho the spectral-radius bound of Theta_V (chasm_step below). */
+enum { CHASM_STRANG = 0, CHASM_LPC1 = 1 };
+
 /* Grid: points per dimension.  nx[d] >= 4; nk[0] = nk[1] = nk[2] in {8, 16, 32}. */
 typedef struct {
   int32_t nx[3];
@@ -103,6 +116,7 @@ typedef struct {
   int32_t use_graphs;   /* 1 (default): chasm_step replays a captured CUDA graph per step   */
   void* cuda_stream;    /* cudaStream_t to run on; NULL: the handle creates its own stream  */
   int32_t theta_form;   /* CHASM_THETA_AUTO (default), CHASM_THETA_TABLE, CHASM_THETA_MODULATED */
+  int32_t integrator;   /* CHASM_STRANG (default) or CHASM_LPC1                              */
 } chasm_options;
 
 /* One initial wavepacket w exp(-ax |x - x0|^2 - ak |k - k0|^2). */
@@ -152,9 +166,12 @@ int chasm_set_stream(chasm_handle* h, void* cuda_stream);
 /* Waits for all work issued on the handle's stream; reports asynchronous CUDA errors. */
 int chasm_sync(chasm_handle* h);
 
-/* nsteps Strang steps S(dt) = A(dt/2) P(dt) A(dt/2) on f_dev, in place, asynchronous on the
- * handle's stream.  dt > 0 and finite, nsteps >= 0.  Coulomb: EUNSTABLE if dt exceeds the
- * Taylor-4 stability bound 2.8 / rho with rho = (2 sum|Z| / (pi^2 hbar)) max|T-hat|. */
+/* nsteps steps of the handle's integrator (Strang: S(dt) = A(dt/2) P(dt) A(dt/2); LPC1: the
+ * predictor-corrector above) on f_dev, in place, asynchronous on the handle's stream.  dt > 0 and
+ * finite, nsteps >= 0.  EUNSTABLE: Strang/Coulomb if dt rho > 2.8 (the Taylor-4 limit on the
+ * imaginary axis is 2 sqrt 2), rho = (2 sum|Z| / (pi^2 hbar)) max|T-hat|; LPC1 if dt rho > 1, rho
+ * as for Strang (Coulomb) or (kappa / hbar) sum_d max_i |x_{d,i} - c_d| pi (N_k/2 - 1) / L_k
+ * (quadratic potential). */
 int chasm_step(chasm_handle* h, void* f_dev, double dt, int32_t nsteps);
 
 /* The two substeps on their own (same layout, in place, asynchronous):
@@ -163,8 +180,10 @@ int chasm_step(chasm_handle* h, void* f_dev, double dt, int32_t nsteps);
 int chasm_advect(chasm_handle* h, void* f_dev, double tau);
 int chasm_pflow(chasm_handle* h, void* f_dev, double dt);
 
-/* out = Theta^T[u] = sum_A -(2 Z_A / (pi^2 hbar)) Im[e^{2i(x-x_A).k} (T * (u e^{-2i(x-x_A).k}))]
- * (Eqs. 4.1, 4.6 with the sign of Eq. 2.3).  Coulomb handles only; u and out must not alias. */
+/* out = Theta_V[u]: Coulomb: sum_A -(2 Z_A / (pi^2 hbar)) Im[e^{2i(x-x_A).k} (T * (u e^{-2i(x-x_A).k}))]
+ * (Eqs. 4.1, 4.6 with the sign of Eq. 2.3); quadratic potential: kappa (x - c)/hbar . grad_k u
+ * (Eq. 5.1, spectral k-derivative without the Nyquist mode).  u and out must not alias; EINVAL for
+ * kappa = 0 without nuclei. */
 int chasm_theta(chasm_handle* h, const void* u_dev, void* out_dev);
 
 /* Mass h1 h2 h3 dk^3 sum f and energy h1 h2 h3 dk^3 sum (hbar^2 |k|^2 / 2m + V(x)) f, both

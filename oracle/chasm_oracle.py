@@ -18,6 +18,8 @@ Grid readings (stated once, used everywhere):
   * k-grid: k_j = (j - N_k/2) dk, dk = 2 L_k / N_k, j = 0..N_k-1 (Sec. 5.2, k_zeta = zeta dk).
   * Strang step S(dt) = A(dt/2) P(dt) A(dt/2); P for the Coulomb case is the 4-term Taylor
     (Horner) approximation of exp(dt Theta^T); for a quadratic potential P is the exact k-shift.
+  * LPC1 step (the paper's one-stage Lawson predictor-corrector): one advection of f and of
+    Theta[f] by the full dt and two applications of Theta (lpc1_step).
   * Sign of the Coulomb operator follows Eq. 2.3 (its classical limit is +(1/hbar) grad V . grad_k f,
     as in Eq. 5.1): Theta = -(2 Z / (pi^2 hbar)) Im[e^{2 i xt.k} Phi], Phi = T * (f e^{-2 i xt.k}).
 
@@ -475,6 +477,82 @@ def run(f: np.ndarray, prob: Problem, dt: float, nsteps: int) -> np.ndarray:
     T = tkm_tensor(prob.nk, prob.lk) if prob.nuclei else None
     for _ in range(nsteps):
         f = strang_step(f, prob, dt, T)
+    return f
+
+
+# --------------------------------------------------------------------------------------------
+# LPC1: the one-stage Lawson predictor-corrector (Sec. 2.2)
+# --------------------------------------------------------------------------------------------
+
+
+def theta_harmonic(f: np.ndarray, prob: Problem) -> np.ndarray:
+    """Theta for V = kappa/2 |x - c|^2: (1/hbar) grad V . grad_k f = sum_d kappa (x_d - c_d)/hbar
+    df/dk_d (Eq. 5.1).  The k-derivative is spectral on the periodic k-grid, i xi_m with
+    xi_m = pi m / L_k, and 0 at the Nyquist mode: the rate at s = 0 of the shift used by
+    pflow_harmonic (whose Nyquist factor cos(xi s) has zero derivative there)."""
+    nk = prob.nk
+    m = np.fft.fftfreq(nk, d=1.0 / nk)
+    ixi = 1j * math.pi * m / prob.lk
+    ixi[nk // 2] = 0.0
+    out = np.zeros_like(f)
+    for d in range(3):
+        deriv = np.real(np.fft.ifft(np.fft.fft(f, axis=3 + d) * ixi.reshape(
+            [nk if a == 3 + d else 1 for a in range(6)]), axis=3 + d))
+        rate = prob.kappa * (prob.xs(d) - prob.center[d]) / prob.hbar
+        out += deriv * rate.reshape([prob.nx[d] if a == d else 1 for a in range(6)])
+    return out
+
+
+def theta(f: np.ndarray, prob: Problem, T=None) -> np.ndarray:
+    """Theta_V[f] for the problem's potential (Coulomb: Sec. 4; quadratic: Eq. 5.1)."""
+    if prob.nuclei:
+        return theta_coulomb(f, prob, T)
+    return theta_harmonic(f, prob)
+
+
+def lpc1_combine(f: np.ndarray, adv, th, dt: float) -> np.ndarray:
+    """The LPC1 combination (Sec. 2.2) for the advection map adv = A(dt), g -> g(A_dt(x, k)) with
+    A_dt(x, k) = (x - hbar k dt / m, k), and the operator th = Theta_V:
+      predictor  f~ = f(A_dt) + dt Theta_V[f](A_dt)
+      corrector  f' = f(A_dt) + dt/2 Theta_V[f~] + dt/2 Theta_V[f](A_dt)."""
+    g = adv(f)
+    h = adv(th(f))
+    ft = g + dt * h
+    return g + 0.5 * dt * th(ft) + 0.5 * dt * h
+
+
+def lpc1_step(f: np.ndarray, prob: Problem, dt: float, T=None) -> np.ndarray:
+    """One LPC1 step on the 6-D grid: lpc1_combine with the advection of Sec. 3 and theta."""
+    if prob.nuclei and T is None:
+        T = tkm_tensor(prob.nk, prob.lk)
+    return lpc1_combine(f, lambda u: advect(u, prob, dt), lambda u: theta(u, prob, T), dt)
+
+
+def lpc1_step_plane(g: np.ndarray, prob: Problem, d: int, dt: float) -> np.ndarray:
+    """One LPC1 step of the quadratic-potential problem on the (x_d, k_d) plane, g[i, j] at
+    (x_{d,i}, k_j): the 1-D spline advection along x_d (Eqs. 3.9, 3.10) and
+    Theta g = kappa (x_d - c_d)/hbar dg/dk spectrally along k (Eq. 5.1), combined by
+    lpc1_combine (the 1-D harmonic oscillator of Sec. 5.1 in its own phase plane)."""
+    nk = prob.nk
+    m = np.fft.fftfreq(nk, d=1.0 / nk)
+    ixi = 1j * math.pi * m / prob.lk
+    ixi[nk // 2] = 0.0
+    rate = prob.kappa * (prob.xs(d) - prob.center[d]) / prob.hbar
+    alpha = prob.hbar * prob.ks() * dt / (prob.m * prob.hs(d))
+
+    def th(gg):
+        return rate[:, None] * np.real(np.fft.ifft(np.fft.fft(gg, axis=1) * ixi[None, :], axis=1))
+
+    def adv(gg):
+        return advect_1d(gg, 0, prob.hs(d), prob.n_nb, alpha, 1)
+
+    return lpc1_combine(g, adv, th, dt)
+
+
+def run_lpc1(f: np.ndarray, prob: Problem, dt: float, nsteps: int) -> np.ndarray:
+    T = tkm_tensor(prob.nk, prob.lk) if prob.nuclei else None
+    for _ in range(nsteps):
+        f = lpc1_step(f, prob, dt, T)
     return f
 
 

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libchasm.so")
 
 OK, PENDING = 0, 1
 THETA_AUTO, THETA_TABLE, THETA_MODULATED = 0, 1, 2
+STRANG, LPC1 = 0, 1
 EINVAL, ENOMEM, ECUDA, EUNSTABLE, EBUSY, EAGAIN, ETIMEOUT, ENOTFOUND, ECANCELED = (
     -1, -2, -3, -4, -5, -6, -7, -8, -9)
 FP32_MIXED, FP64 = 0, 1
@@ -44,7 +45,8 @@ class Potential(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("n_nb", C.c_int32), ("patches", C.c_int32 * 3),
-                ("use_graphs", C.c_int32), ("cuda_stream", C.c_void_p), ("theta_form", C.c_int32)]
+                ("use_graphs", C.c_int32), ("cuda_stream", C.c_void_p), ("theta_form", C.c_int32),
+                ("integrator", C.c_int32)]
 
 
 class Gaussian(C.Structure):
@@ -165,7 +167,7 @@ class Solver:
 
     def __init__(self, nx, nk, x_lo, x_hi, lk, nuclei=(), kappa=0.0, center=(0.0, 0.0, 0.0),
                  hbar=1.0, m=1.0, precision=FP32_MIXED, n_nb=20, use_graphs=True, stream=None,
-                 theta_form=THETA_AUTO):
+                 theta_form=THETA_AUTO, integrator=STRANG):
         L = lib()
         self._tstream = None
         if stream is None:
@@ -189,6 +191,7 @@ class Solver:
         opt.use_graphs = 1 if use_graphs else 0
         opt.cuda_stream = stream if stream is not None else None
         opt.theta_form = theta_form
+        opt.integrator = integrator
         self.opt = opt
         h = C.c_void_p()
         _check(L.chasm_create(C.byref(self.grid), C.byref(self.box), C.byref(self.pot), hbar, m,
@@ -292,7 +295,7 @@ class Solver:
 
 
 def workspace_bytes(nx, nk, nuclei=(), kappa=0.0, precision=FP32_MIXED, n_nb=20,
-                    theta_form=THETA_AUTO) -> int:
+                    theta_form=THETA_AUTO, integrator=STRANG) -> int:
     L = lib()
     g = make_grid(nx, nk)
     nuc = (Nucleus * max(1, len(nuclei)))(*[Nucleus((C.c_double * 3)(*p), z) for p, z in nuclei])
@@ -302,6 +305,7 @@ def workspace_bytes(nx, nk, nuclei=(), kappa=0.0, precision=FP32_MIXED, n_nb=20,
     opt.precision = precision
     opt.n_nb = n_nb
     opt.theta_form = theta_form
+    opt.integrator = integrator
     return L.chasm_workspace_bytes(C.byref(g), C.byref(pot), C.byref(opt))
 
 

@@ -79,6 +79,8 @@ std::string validate(const chasm_grid* grid, const chasm_box* box, const chasm_p
     if (opt->theta_form != CHASM_THETA_AUTO && opt->theta_form != CHASM_THETA_TABLE &&
         opt->theta_form != CHASM_THETA_MODULATED)
       return "options: theta_form must be CHASM_THETA_AUTO, _TABLE or _MODULATED";
+    if (opt->integrator != CHASM_STRANG && opt->integrator != CHASM_LPC1)
+      return "options: integrator must be CHASM_STRANG or CHASM_LPC1";
   }
   return std::string();
 }
@@ -99,6 +101,7 @@ chasm_options defaults() {
   o.use_graphs = 1;
   o.cuda_stream = nullptr;
   o.theta_form = CHASM_THETA_AUTO;
+  o.integrator = CHASM_STRANG;
   return o;
 }
 
@@ -477,8 +480,56 @@ int do_pflow(Handle* H, void* f, double dt) {
   return CHASM_OK;
 }
 
+// Spectral-radius bound of Theta for the quadratic potential: the rate kappa |x_d - c_d| / hbar
+// times the largest kept k-frequency pi (N/2 - 1) / L_k, summed over d.
+double harmonic_rho(const Handle* H) {
+  double r = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double lo = H->g.x_lo[d], hi = lo + (H->g.nx[d] - 1) * H->g.h[d];
+    r += std::max(std::fabs(lo - H->center[d]), std::fabs(hi - H->center[d]));
+  }
+  return std::fabs(H->kappa) / H->hbar * r * M_PI * (H->g.nk / 2 - 1) / H->g.lk;
+}
+
+// out = (base or 0) + c Theta_V[in] for either potential and either Coulomb form; in != out
+int theta_any(Handle* H, const void* in, const void* base, void* out, double c) {
+  if (H->nuclei.empty()) {
+    CHASM_CUDA(H, launch_theta_harm(*H, in, base, out, c, H->stream));
+  } else if (H->xs) {
+    CHASM_CUDA(H, launch_theta_xs(*H, in, base, out, 1, &c, H->stream));
+  } else {
+    double coef[kMaxNuclei];
+    for (size_t a = 0; a < H->nuclei.size(); ++a)
+      coef[a] = -(2.0 * H->nuclei[a].charge / (M_PI * M_PI * H->hbar)) * c;
+    CHASM_CUDA(H, launch_theta(*H, in, base, out, coef, H->stream));
+  }
+  return CHASM_OK;
+}
+
+// One LPC1 step (Sec. 2.2): U = Theta f; advect f (= g) and U (= h) by dt; V = g + dt h (the
+// predictor), f = g + dt/2 h; f += dt/2 Theta V.
+int issue_step_lpc1(Handle* H, void* f, double dt) {
+  void* U = H->d_u[0];
+  void* V = H->d_u[1];
+  int rc = theta_any(H, f, nullptr, U, 1.0);
+  if (rc) return rc;
+  rc = do_advect(H, f, dt, true);
+  if (rc) return rc;
+  rc = do_advect(H, U, dt, true);
+  if (rc) return rc;
+  CHASM_CUDA(H, launch_lpc1_combine(*H, f, U, V, dt, H->stream));
+  return theta_any(H, V, f, f, 0.5 * dt);
+}
+
 int prepare_step(Handle* H, double dt) {
   if (!is_finite(dt) || !(dt > 0)) return fail(H, CHASM_EINVAL, "dt must be > 0 and finite");
+  if (H->opt.integrator == CHASM_LPC1) {
+    const double rho = H->nuclei.empty() ? harmonic_rho(H) : coulomb_rho(H);
+    if (dt * rho > 1.0)
+      return fail(H, CHASM_EUNSTABLE, "dt * rho(Theta) = " + std::to_string(dt * rho) +
+                                          " exceeds the LPC1 limit 1");
+    return ensure_advect_tables(H, dt);
+  }
   if (!H->nuclei.empty() && dt * coulomb_rho(H) > 2.8)
     return fail(H, CHASM_EUNSTABLE,
                 "dt * rho(Theta^T) = " + std::to_string(dt * coulomb_rho(H)) +
@@ -493,6 +544,7 @@ int prepare_step(Handle* H, double dt) {
 }
 
 int issue_step(Handle* H, void* f, double dt) {
+  if (H->opt.integrator == CHASM_LPC1) return issue_step_lpc1(H, f, dt);
   int rc = do_advect(H, f, 0.5 * dt, true);
   if (rc) return rc;
   rc = do_pflow(H, f, dt);
@@ -549,6 +601,9 @@ size_t chasm_workspace_bytes(const chasm_grid* grid, const chasm_potential* pot,
     }
     w += tp.scratch_bytes;
     w += (size_t)8 * nk * nk * nk * e + (size_t)(2 * nk - 1) * (2 * nk - 1) * (2 * nk - 1) * 8;
+    if (xs && o.integrator == CHASM_LPC1) w += 2 * fbytes;
+  } else if (o.integrator == CHASM_LPC1) {
+    w += 2 * fbytes;
   }
   w += (size_t)nxp * 8 + 3 * (size_t)moments_blocks() * 8 + 64;
   w += (size_t)3 * (grid->nx[0] + grid->nx[1] + grid->nx[2]) * (8 + 2 * e);
@@ -658,6 +713,11 @@ int chasm_create(const chasm_grid* grid, const chasm_box* box, const chasm_poten
           cudaMallocAsync(&H->d_u[1], fbytes, H->stream) != cudaSuccess)
         return bail(fail(H, CHASM_ENOMEM, "device allocation failed (Horner buffers / scratch)"));
     }
+  }
+  if (o.integrator == CHASM_LPC1 && !H->d_u[0]) {   // the two LPC1 work copies of f
+    if (cudaMallocAsync(&H->d_u[0], fbytes, H->stream) != cudaSuccess ||
+        cudaMallocAsync(&H->d_u[1], fbytes, H->stream) != cudaSuccess)
+      return bail(fail(H, CHASM_ENOMEM, "device allocation failed (LPC1 buffers)"));
   }
   e = cudaStreamSynchronize(H->stream);
   if (e != cudaSuccess) return bail(cuda_fail(H, e, "create"));
@@ -773,21 +833,13 @@ int chasm_pflow(chasm_handle* h, void* f, double dt) {
 int chasm_theta(chasm_handle* h, const void* u, void* out) {
   Handle* H = reinterpret_cast<Handle*>(h);
   if (!H) return fail(nullptr, CHASM_EINVAL, "handle is NULL");
-  if (H->nuclei.empty()) return fail(H, CHASM_EINVAL, "chasm_theta needs a Coulomb potential");
+  if (H->nuclei.empty() && H->kappa == 0.0)
+    return fail(H, CHASM_EINVAL, "chasm_theta needs a Coulomb or a quadratic potential (kappa != 0)");
   if (!u || !out) return fail(H, CHASM_EINVAL, "u/out is NULL");
   if (u == out) return fail(H, CHASM_EINVAL, "u and out must not alias");
   if (((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(out)) & 15) != 0)
     return fail(H, CHASM_EINVAL, "u/out must be 16-byte aligned");
-  if (H->xs) {
-    const double one = 1.0;
-    CHASM_CUDA(H, launch_theta_xs(*H, u, nullptr, out, 1, &one, H->stream));
-    return CHASM_OK;
-  }
-  double coef[kMaxNuclei];
-  for (size_t a = 0; a < H->nuclei.size(); ++a)
-    coef[a] = -(2.0 * H->nuclei[a].charge / (M_PI * M_PI * H->hbar));
-  CHASM_CUDA(H, launch_theta(*H, u, nullptr, out, coef, H->stream));
-  return CHASM_OK;
+  return theta_any(H, u, nullptr, out, 1.0);
 }
 
 int chasm_moments(chasm_handle* h, const void* f, double* mass, double* energy) {

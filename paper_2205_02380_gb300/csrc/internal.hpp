@@ -59,6 +59,12 @@ void theta_plan(int nk, bool fp64, int64_t nxp, int num_sms, ThetaPlan* plan);
 cudaError_t launch_theta_xs(const Handle& H, const void* in, const void* base, void* out, int nst,
                             const double* coef, cudaStream_t s);
 void theta_xs_plan(int nk, bool fp64, int64_t nxp, int num_sms, ThetaPlan* plan);
+// LPC1 (k_lpc1.cu): Theta of the quadratic potential, out = (base or 0) + coef Theta[in]
+// (in must not alias out), and the predictor/corrector combination v = f + dt h, f = f + dt/2 h
+cudaError_t launch_theta_harm(const Handle& H, const void* in, const void* base, void* out,
+                              double coef, cudaStream_t s);
+cudaError_t launch_lpc1_combine(const Handle& H, void* f, const void* h, void* v, double dt,
+                                cudaStream_t s);
 // the per-x symbol table (k_xsym.cu), [nxp][N][2N][2N] in the storage type; needs H.d_T
 size_t xs_table_bytes(int nk, int64_t nxp, size_t elt);
 cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s);

@@ -1,0 +1,157 @@
+// Kernels of the LPC1 integrator (Sec. 2.2) that the Strang step does not have:
+//
+//   k_kderiv        Theta for V = kappa/2 |x - c|^2 (Eq. 5.1), one k-dimension per launch:
+//                   out = (base or out) + coef kappa (x_d - c_d)/hbar D u along k_d, where D is the
+//                   spectral derivative on the periodic k-grid (i xi_m, xi_m = pi m / L_k, the
+//                   Nyquist mode dropped), applied as its circulant: (D u)_p = sum_j d_j u_{p-j},
+//                   d_j = -(2/N) sum_{m=1}^{N/2-1} xi_m sin(2 pi m j / N).  One thread per k-line,
+//                   the N taps in the kernel's parameter block (constant-bank operands).
+//   k_lpc1_combine  predictor and corrector base from the advected fields g = f(A_dt) and
+//                   h = Theta[f](A_dt): v = g + dt h (the predictor f~), f = g + dt/2 h.
+#include "internal.hpp"
+
+namespace chasm {
+namespace {
+
+template <typename T, int N>
+struct KDerivParams {
+  const T* in;
+  const T* base;     // first dimension: out = base + ...; null: out = ...
+  T* out;
+  int64_t nxp;
+  int nx1, nx2, nx3;
+  int dim;
+  bool accumulate;   // out += ...
+  double x_lo, h, center, rate_scale;   // rate(x_d) = rate_scale (x_lo + i h - center)
+  T coef;
+  T d[N];
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_kderiv(const KDerivParams<T, N> p) {
+  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= p.nxp * N * N) return;
+  const int64_t xp = line / (N * N);
+  const int r = (int)(line % (N * N));
+  int64_t base, stride;
+  int id;
+  if (p.dim == 0) {
+    base = xp * N * N * N + r;
+    stride = N * N;
+    id = (int)(xp / ((int64_t)p.nx2 * p.nx3));
+  } else if (p.dim == 1) {
+    base = xp * N * N * N + (r / N) * N * N + (r % N);
+    stride = N;
+    id = (int)((xp / p.nx3) % p.nx2);
+  } else {
+    base = xp * N * N * N + (int64_t)r * N;
+    stride = 1;
+    id = (int)(xp % p.nx3);
+  }
+  const T scale = (T)(p.rate_scale * (p.x_lo + id * p.h - p.center)) * p.coef;
+  T v[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) v[l] = p.in[base + l * stride];
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    T acc = (T)0;
+#pragma unroll
+    for (int l = 0; l < N; ++l) acc = fma(p.d[(q - l + N) & (N - 1)], v[l], acc);
+    const int64_t o = base + q * stride;
+    T b = (T)0;
+    if (p.accumulate)
+      b = p.out[o];
+    else if (p.base)
+      b = p.base[o];
+    p.out[o] = fma(scale, acc, b);
+  }
+}
+
+template <typename T>
+__global__ void k_lpc1_combine(T* __restrict__ f, const T* __restrict__ h, T* __restrict__ v, int64_t n,
+                               T dt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const T half = dt * (T)0.5;
+  if constexpr (sizeof(T) == 4) {
+    if (4 * i >= n) return;   // n is a multiple of 4 (N_k^3 per x point)
+    const float4 g4 = reinterpret_cast<const float4*>(f)[i];
+    const float4 h4 = reinterpret_cast<const float4*>(h)[i];
+    reinterpret_cast<float4*>(v)[i] = make_float4(fmaf(dt, h4.x, g4.x), fmaf(dt, h4.y, g4.y),
+                                                  fmaf(dt, h4.z, g4.z), fmaf(dt, h4.w, g4.w));
+    reinterpret_cast<float4*>(f)[i] = make_float4(fmaf(half, h4.x, g4.x), fmaf(half, h4.y, g4.y),
+                                                  fmaf(half, h4.z, g4.z), fmaf(half, h4.w, g4.w));
+  } else {
+    if (2 * i >= n) return;
+    const double2 g2 = reinterpret_cast<const double2*>(f)[i];
+    const double2 h2 = reinterpret_cast<const double2*>(h)[i];
+    reinterpret_cast<double2*>(v)[i] = make_double2(fma(dt, h2.x, g2.x), fma(dt, h2.y, g2.y));
+    reinterpret_cast<double2*>(f)[i] = make_double2(fma(half, h2.x, g2.x), fma(half, h2.y, g2.y));
+  }
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename T, int N>
+cudaError_t kderiv_tn(const Handle& H, const void* in, const void* base, void* out, double coef,
+                      cudaStream_t s) {
+  KDerivParams<T, N> p;
+  p.in = static_cast<const T*>(in);
+  p.base = static_cast<const T*>(base);
+  p.out = static_cast<T*>(out);
+  p.nxp = H.g.nxp;
+  p.nx1 = H.g.nx[0];
+  p.nx2 = H.g.nx[1];
+  p.nx3 = H.g.nx[2];
+  p.coef = (T)coef;
+  p.rate_scale = H.kappa / H.hbar;
+  for (int j = 0; j < N; ++j) {
+    double acc = 0.0;
+    for (int m = 1; m < N / 2; ++m)
+      acc += (M_PI * m / H.g.lk) * std::sin(2.0 * M_PI * m * j / N);
+    p.d[j] = (T)(-2.0 * acc / N);
+  }
+  const unsigned nb = nblk(H.g.nxp * N * N, 128);
+  for (int d = 0; d < 3; ++d) {
+    p.dim = d;
+    p.accumulate = d > 0;
+    p.x_lo = H.g.x_lo[d];
+    p.h = H.g.h[d];
+    p.center = H.center[d];
+    k_kderiv<T, N><<<nb, 128, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_theta_harm(const Handle& H, const void* in, const void* base, void* out,
+                              double coef, cudaStream_t s) {
+  switch (H.g.nk) {
+    case 8:
+      return H.fp64 ? kderiv_tn<double, 8>(H, in, base, out, coef, s)
+                    : kderiv_tn<float, 8>(H, in, base, out, coef, s);
+    case 16:
+      return H.fp64 ? kderiv_tn<double, 16>(H, in, base, out, coef, s)
+                    : kderiv_tn<float, 16>(H, in, base, out, coef, s);
+    case 32:
+      return H.fp64 ? kderiv_tn<double, 32>(H, in, base, out, coef, s)
+                    : kderiv_tn<float, 32>(H, in, base, out, coef, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lpc1_combine(const Handle& H, void* f, const void* h, void* v, double dt,
+                                cudaStream_t s) {
+  const int64_t n = H.g.ncell;
+  if (H.fp64) {
+    k_lpc1_combine<double><<<nblk(n / 2, 256), 256, 0, s>>>((double*)f, (const double*)h, (double*)v, n, dt);
+  } else {
+    k_lpc1_combine<float><<<nblk(n / 4, 256), 256, 0, s>>>((float*)f, (const float*)h, (float*)v, n,
+                                                             (float)dt);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace chasm

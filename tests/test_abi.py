@@ -52,12 +52,12 @@ def test_options_default(ch):
     o = ch.Options()
     assert ch.lib().chasm_options_default(C.byref(o)) == 0
     assert (o.precision, o.n_nb, list(o.patches), o.use_graphs) == (ch.FP32_MIXED, 20, [1, 1, 1], 1)
-    assert o.theta_form == ch.THETA_AUTO
+    assert o.theta_form == ch.THETA_AUTO and o.integrator == ch.STRANG
     assert ch.lib().chasm_options_default(None) == ch.EINVAL
 
 
 def _create(ch, nx=(8, 8, 8), nk=16, lo=-4.0, hi=4.0, lk=4.0, nuclei=(), hbar=1.0, m=1.0,
-            precision=0, n_nb=20, patches=(1, 1, 1), theta_form=0):
+            precision=0, n_nb=20, patches=(1, 1, 1), theta_form=0, integrator=0):
     L = ch.lib()
     g = ch.make_grid(list(nx), nk) if not isinstance(nk, tuple) else ch.Grid(
         (C.c_int32 * 3)(*nx), (C.c_int32 * 3)(*nk))
@@ -70,6 +70,7 @@ def _create(ch, nx=(8, 8, 8), nk=16, lo=-4.0, hi=4.0, lk=4.0, nuclei=(), hbar=1.
     o.n_nb = n_nb
     o.patches = (C.c_int32 * 3)(*patches)
     o.theta_form = theta_form
+    o.integrator = integrator
     h = C.c_void_p()
     rc = L.chasm_create(C.byref(g), C.byref(b), C.byref(pot), hbar, m, C.byref(o), C.byref(h))
     return rc, L.chasm_last_error(None).decode()
@@ -89,6 +90,7 @@ def _create(ch, nx=(8, 8, 8), nk=16, lo=-4.0, hi=4.0, lk=4.0, nuclei=(), hbar=1.
     (dict(patches=(7, 1, 1), nx=(8, 8, 8)), "patches"),
     (dict(nuclei=[((float("nan"), 0, 0), 1.0)]), "nucleus"),
     (dict(theta_form=3), "theta_form"),
+    (dict(integrator=2), "integrator"),
 ])
 def test_create_rejects_invalid_arguments_on_the_host(ch, kw, needle):
     rc, msg = _create(ch, **kw)
@@ -122,6 +124,13 @@ def test_workspace_bytes_of_the_two_theta_forms(ch):
     big_tab = ch.workspace_bytes(64, 32, nuclei=nuc, theta_form=ch.THETA_TABLE)
     assert big_tab >= 4 * 64 ** 3 * 32 ** 3 * 4
     assert ch.workspace_bytes(64, 32, nuclei=nuc) < big_tab
+    # LPC1 adds two work copies of f to the table form and to the quadratic potential
+    assert ch.workspace_bytes(16, 16, nuclei=nuc, theta_form=ch.THETA_TABLE,
+                              integrator=ch.LPC1) == w_tab + 2 * f
+    assert ch.workspace_bytes(16, 16, nuclei=nuc, theta_form=ch.THETA_MODULATED,
+                              integrator=ch.LPC1) == w_mod
+    w_h = ch.workspace_bytes(16, 16, kappa=1.0)
+    assert ch.workspace_bytes(16, 16, kappa=1.0, integrator=ch.LPC1) == w_h + 2 * f
 
 
 def test_null_handles_are_rejected(ch):
