@@ -144,10 +144,32 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------
-def make_solver(ch, precision, stream):
+def make_solver(ch, precision, stream, integrator=None):
     W = WORKLOAD
     return ch.Solver(W["nx"], W["nk"], -W["L"], W["L"], W["lk"], nuclei=W["nuclei"],
-                     precision=precision, stream=stream.cuda_stream, theta_form=ch.THETA_TABLE)
+                     precision=precision, stream=stream.cuda_stream, theta_form=ch.THETA_TABLE,
+                     integrator=ch.STRANG if integrator is None else integrator)
+
+
+def time_lpc1(torch, ch, stream, steps, warmup):
+    """The paper's LPC1 integrator on the same workload (FP32-mixed, table form): W untimed and
+    `steps` timed steps, CUDA events on the solver's stream."""
+    W = WORKLOAD
+    with torch.cuda.stream(stream):
+        s = make_solver(ch, ch.FP32_MIXED, stream, ch.LPC1)
+        f = torch.empty((W["nx"],) * 3 + (W["nk"],) * 3, device="cuda", dtype=torch.float32)
+        s.init_hydrogen_1s(f, n_y=W["n_y"])
+        m0 = s.mass(f)
+        ms = time_steps(torch, s, f, W["dt"], steps, warmup, stream, None)
+        m1 = s.mass(f)
+        s.close()
+        del f
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    cells = W["nx"] ** 3 * W["nk"] ** 3
+    return {"value": cells * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "dtype": "f32", "mass_drift": (m1 - m0) / m0,
+            "note": "LPC1 (Sec. 2.2): 2 Theta applications, 6 advection passes, 1 combine per step"}
 
 
 def aggregate_ranks(ms_local: float, cells: int, steps: int, dist=None, device="cpu"):
@@ -353,6 +375,7 @@ def run_chasm(args):
         result[prec_name] = entry
 
     accuracy = accuracy_check(torch, ch, stream, args.acc_steps) if rank == 0 else None
+    lpc1 = time_lpc1(torch, ch, stream, max(1, args.steps), 1) if rank == 0 and not args.no_lpc1 else None
     serving = None
     if rank == 0 and not args.no_serving:
         serving = run_serving(ch, n_req=16, rate=20.0, seed=2205, nx_choices=(16, 24),
@@ -381,6 +404,7 @@ def run_chasm(args):
         "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
                  "dtype": "f64"},
         "accuracy": accuracy,
+        "lpc1": lpc1,
         "serving": serving,
         "roofline": {"kernel": "k_theta_xs (P(dt): four Horner stages of Theta^T per x point, "
                                "table form)",
@@ -536,6 +560,7 @@ def main():
     ap.add_argument("--nx", type=int, default=None, help="override N_x (profiling on smaller cases)")
     ap.add_argument("--acc-steps", type=int, default=4)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-lpc1", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--rate", type=float, default=5.0)
     ap.add_argument("--slots", type=int, default=8)
