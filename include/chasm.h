@@ -63,8 +63,8 @@ enum { CHASM_FP32_MIXED = 0, CHASM_FP64 = 1 };
  *     stages per x point in one kernel and needs no Horner buffers.
  *   CHASM_THETA_MODULATED: the complex form of Eq. 4.6 per nucleus (modulate by e^{-2i(x-x_A).k},
  *     convolve with T, demodulate, imaginary part); workspace two copies of f.
- *   CHASM_THETA_AUTO (default): the table form when the table needs at most 64 GiB, else the
- *     modulated form. */
+ *   CHASM_THETA_AUTO (default): the table form when the table needs at most half of the current
+ *     device's memory (64 GiB when no device can be queried), else the modulated form. */
 enum { CHASM_THETA_AUTO = 0, CHASM_THETA_TABLE = 1, CHASM_THETA_MODULATED = 2 };
 
 /* Time integrator of chasm_step (chasm_options.integrator).

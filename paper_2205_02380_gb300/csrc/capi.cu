@@ -85,12 +85,28 @@ std::string validate(const chasm_grid* grid, const chasm_box* box, const chasm_p
   return std::string();
 }
 
-// Whether the Coulomb operator uses the per-x symbol table (CHASM_THETA_AUTO: table up to
-// kXsAutoMaxBytes).
+// CHASM_THETA_AUTO limit: half of the current device's memory (kXsAutoMaxBytes when the device
+// cannot be queried), looked up once per device.
+size_t auto_table_limit() {
+  static std::mutex mu;
+  static size_t limit[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kXsAutoMaxBytes;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!limit[dev]) {
+    cudaDeviceProp prop;
+    limit[dev] = cudaGetDeviceProperties(&prop, dev) == cudaSuccess && prop.totalGlobalMem > 0
+                     ? prop.totalGlobalMem / 2
+                     : kXsAutoMaxBytes;
+  }
+  return limit[dev];
+}
+
+// Whether the Coulomb operator uses the per-x symbol table.
 bool table_form(int nk, int64_t nxp, size_t elt, const chasm_options& o) {
   if (o.theta_form == CHASM_THETA_TABLE) return true;
   if (o.theta_form == CHASM_THETA_MODULATED) return false;
-  return xs_table_bytes(nk, nxp, elt) <= kXsAutoMaxBytes;
+  return xs_table_bytes(nk, nxp, elt) <= auto_table_limit();
 }
 
 chasm_options defaults() {

@@ -68,7 +68,7 @@ cudaError_t launch_lpc1_combine(const Handle& H, void* f, const void* h, void* v
 // the per-x symbol table (k_xsym.cu), [nxp][N][2N][2N] in the storage type; needs H.d_T
 size_t xs_table_bytes(int nk, int64_t nxp, size_t elt);
 cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s);
-constexpr size_t kXsAutoMaxBytes = (size_t)64 << 30;   // CHASM_THETA_AUTO: table form up to 64 GiB
+constexpr size_t kXsAutoMaxBytes = (size_t)64 << 30;   // CHASM_THETA_AUTO limit without a device
 // symbol precompute (k_symbol.cu): T (FP64, (2N-1)^3) and T-hat (parity-major, scaled)
 cudaError_t compute_symbol(int nk, double lk, double* T_dev, void* that_dev, bool fp64,
                            double* that_absmax_host, cudaStream_t s);

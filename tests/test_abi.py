@@ -111,7 +111,7 @@ def test_workspace_bytes(ch):
 def test_workspace_bytes_of_the_two_theta_forms(ch):
     """Coulomb workspace: the table form holds 4 N_k^3 values per x point (four copies of f) and
     no Horner buffers; the modulated form two Horner buffers; AUTO picks the table when it needs
-    at most 64 GiB."""
+    at most half of the device's memory (64 GiB when no device can be queried, as here)."""
     nuc = [((0.0, 0.0, 0.0), 1.0)]
     f = 16 ** 6 * 4
     w_tab = ch.workspace_bytes(16, 16, nuclei=nuc, theta_form=ch.THETA_TABLE)
