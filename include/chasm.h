@@ -192,6 +192,19 @@ int chasm_mass(chasm_handle* h, const void* f_dev, double* out);
 int chasm_energy(chasm_handle* h, const void* f_dev, double* out);
 int chasm_moments(chasm_handle* h, const void* f_dev, double* mass, double* energy);
 
+/* Phase-space diagnostics of Sec. 5, accumulated in FP64 in a fixed order (bitwise reproducible),
+ * synchronous; f_dev as in chasm_step, results in host memory:
+ *   chasm_reduced_wigner: W_j(x, k) = integral of f over the other two x and the other two k
+ *     coordinates (grid sums times their cell volume), j in {0, 1, 2}; w_host[i][q] for the
+ *     nx[j] x N_k nodes (x_{j,i}, k_q), row-major;
+ *   chasm_marginal_x12: the spatial marginal P(x1, x2) = integral over x3 and k; p_host[i1][i2],
+ *     nx[0] x nx[1];
+ *   chasm_expectations: out_host[0..2] = <x_d> = sum x_d f / sum f and out_host[3..5] = <k_d>
+ *     (the averaged position and momentum). */
+int chasm_reduced_wigner(chasm_handle* h, const void* f_dev, int32_t j, double* w_host);
+int chasm_marginal_x12(chasm_handle* h, const void* f_dev, double* p_host);
+int chasm_expectations(chasm_handle* h, const void* f_dev, double* out_host);
+
 /* Mass and energy exactly as chasm_moments defines them, for callers that cannot allocate
  * device memory when they need them: code running while a stream is captured in the global
  * capture mode (cudaMalloc is not allowed then), services that reserve their whole memory budget

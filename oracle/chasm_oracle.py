@@ -579,6 +579,34 @@ def energy(f: np.ndarray, prob: Problem) -> float:
     return float((kin + pot) * cell_volume(prob))
 
 
+def reduced_wigner(f: np.ndarray, prob: Problem, j: int) -> np.ndarray:
+    """W_j(x, k) = integral of f over the other two x and the other two k coordinates (Sec. 5),
+    on the grid: the sum over those indices times their cell volume; shape (nx_j, N_k)."""
+    others = [d for d in range(3) if d != j]
+    vol = prob.hs(others[0]) * prob.hs(others[1]) * prob.dk ** 2
+    return np.sum(f, axis=tuple(others) + tuple(3 + d for d in others)) * vol
+
+
+def marginal_x12(f: np.ndarray, prob: Problem) -> np.ndarray:
+    """P(x1, x2) = integral of f over x3 and k (Sec. 5); shape (nx_1, nx_2)."""
+    return np.sum(f, axis=(2, 3, 4, 5)) * prob.hs(2) * prob.dk ** 3
+
+
+def expectations(f: np.ndarray, prob: Problem) -> np.ndarray:
+    """<x_d> and <k_d>, d = 1..3: the f-weighted grid averages sum(x_d f) / sum(f) and
+    sum(k_d f) / sum(f) (the averaged position and momentum of Sec. 5.3)."""
+    tot = np.sum(f)
+    out = np.zeros(6)
+    for d in range(3):
+        shape = [1] * 6
+        shape[d] = prob.nx[d]
+        out[d] = np.sum(f * prob.xs(d).reshape(shape)) / tot
+        shape = [1] * 6
+        shape[3 + d] = prob.nk
+        out[3 + d] = np.sum(f * prob.ks().reshape(shape)) / tot
+    return out
+
+
 def errors(f_ref: np.ndarray, f_num: np.ndarray, prob: Problem):
     """(eps_inf, eps_2) of Sec. 5 with the integral as the grid sum times the cell volume."""
     d = f_ref - f_num

@@ -88,6 +88,9 @@ _SIGS = [
     ("chasm_mass", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("chasm_energy", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("chasm_moments", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("chasm_reduced_wigner", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double)]),
+    ("chasm_marginal_x12", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    ("chasm_expectations", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("chasm_moments_noalloc", C.c_int, [C.c_void_p, C.POINTER(Grid), C.POINTER(Box), C.POINTER(Potential),
                                         C.c_double, C.c_double, C.c_int32, C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -275,6 +278,26 @@ class Solver:
         e = C.c_double()
         self._call(lib().chasm_energy, _ptr(f), C.byref(e))
         return e.value
+
+    def reduced_wigner(self, f, j):
+        """W_j as a (nx[j], N_k) float64 numpy array."""
+        import numpy as np
+        out = np.zeros((self.shape[j], self.shape[3]))
+        self._call(lib().chasm_reduced_wigner, _ptr(f), j,
+                   out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
+
+    def marginal_x12(self, f):
+        import numpy as np
+        out = np.zeros((self.shape[0], self.shape[1]))
+        self._call(lib().chasm_marginal_x12, _ptr(f), out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
+
+    def expectations(self, f):
+        """(<x_1>, <x_2>, <x_3>, <k_1>, <k_2>, <k_3>)."""
+        out = (C.c_double * 6)()
+        self._call(lib().chasm_expectations, _ptr(f), out)
+        return tuple(out)
 
     def init_gaussians(self, f, packets):
         arr = (Gaussian * len(packets))(*[make_gaussian(p["w"], p["x0"], p["k0"], p["ax"], p["ak"])

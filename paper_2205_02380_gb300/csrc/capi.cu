@@ -447,7 +447,7 @@ void free_all(Handle* H) {
   H->graph = nullptr;
   void* ptrs[] = {H->d_clos[0], H->d_clos[1], H->d_clos[2], H->d_lu[0], H->d_lu[1], H->d_lu[2], H->adv.dev, H->d_T,
                   H->d_that, H->d_phase, H->d_sig, H->d_scratch, H->d_u[0], H->d_u[1], H->d_krows,
-                  H->d_partials, H->d_result, H->d_vx, H->d_fhost};
+                  H->d_partials, H->d_result, H->d_vx, H->d_diag, H->d_fhost};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, H->stream);
   if (H->stream) cudaStreamSynchronize(H->stream);
@@ -622,6 +622,7 @@ size_t chasm_workspace_bytes(const chasm_grid* grid, const chasm_potential* pot,
     w += 2 * fbytes;
   }
   w += (size_t)nxp * 8 + 3 * (size_t)moments_blocks() * 8 + 64;
+  w += diag_bytes(grid->nx, nk);
   w += (size_t)3 * (grid->nx[0] + grid->nx[1] + grid->nx[2]) * (8 + 2 * e);
   w += (size_t)(grid->nx[0] + grid->nx[1] + grid->nx[2]) * nk * e + 3 * nk * (4 * e + 4);
   return w;
@@ -698,7 +699,8 @@ int chasm_create(const chasm_grid* grid, const chasm_box* box, const chasm_poten
   rc = build_potential_table(H);
   if (rc) return bail(rc);
   if (cudaMallocAsync((void**)&H->d_partials, sizeof(double) * 3 * moments_blocks(), H->stream) != cudaSuccess ||
-      cudaMallocAsync((void**)&H->d_result, sizeof(double) * 4, H->stream) != cudaSuccess)
+      cudaMallocAsync((void**)&H->d_result, sizeof(double) * 4, H->stream) != cudaSuccess ||
+      cudaMallocAsync((void**)&H->d_diag, diag_bytes(g.nx, g.nk), H->stream) != cudaSuccess)
     return bail(fail(H, CHASM_ENOMEM, "device allocation failed (reductions)"));
   const size_t fbytes = (size_t)g.ncell * H->elt;
   if (!H->nuclei.empty()) {
@@ -869,6 +871,34 @@ int chasm_moments(chasm_handle* h, const void* f, double* mass, double* energy) 
   if (mass) *mass = r[0];
   if (energy) *energy = r[1];
   return CHASM_OK;
+}
+
+namespace {
+int diag_call(chasm_handle* h, const void* f, int what, int j, double* out, size_t n) {
+  Handle* H = reinterpret_cast<Handle*>(h);
+  if (!H) return fail(nullptr, CHASM_EINVAL, "handle is NULL");
+  if (!f || !out) return fail(H, CHASM_EINVAL, "f/out is NULL");
+  double* res = H->d_diag + (size_t)3 * H->g.nxp * H->g.nk;
+  CHASM_CUDA(H, launch_diag(*H, f, what, j, H->d_diag, res, H->stream));
+  CHASM_CUDA(H, cudaMemcpyAsync(out, res, n * sizeof(double), cudaMemcpyDeviceToHost, H->stream));
+  CHASM_CUDA(H, cudaStreamSynchronize(H->stream));
+  return CHASM_OK;
+}
+}  // namespace
+
+int chasm_reduced_wigner(chasm_handle* h, const void* f, int32_t j, double* w_host) {
+  Handle* H = reinterpret_cast<Handle*>(h);
+  if (H && (j < 0 || j > 2)) return fail(H, CHASM_EINVAL, "j must be 0, 1 or 2");
+  return diag_call(h, f, 0, j, w_host, H ? (size_t)H->g.nx[j < 0 || j > 2 ? 0 : j] * H->g.nk : 0);
+}
+
+int chasm_marginal_x12(chasm_handle* h, const void* f, double* p_host) {
+  Handle* H = reinterpret_cast<Handle*>(h);
+  return diag_call(h, f, 1, 0, p_host, H ? (size_t)H->g.nx[0] * H->g.nx[1] : 0);
+}
+
+int chasm_expectations(chasm_handle* h, const void* f, double* out_host) {
+  return diag_call(h, f, 2, 0, out_host, 6);
 }
 
 int chasm_mass(chasm_handle* h, const void* f, double* out) {

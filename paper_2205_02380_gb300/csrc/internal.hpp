@@ -65,6 +65,11 @@ cudaError_t launch_theta_harm(const Handle& H, const void* in, const void* base,
                               double coef, cudaStream_t s);
 cudaError_t launch_lpc1_combine(const Handle& H, void* f, const void* h, void* v, double dt,
                                 cudaStream_t s);
+// phase-space diagnostics (k_diag.cu): what = 0 reduced Wigner W_j, 1 marginal P(x1, x2),
+// 2 averages <x_d>, <k_d>; buf holds diag_bytes of FP64 scratch, out_dev the result
+size_t diag_bytes(const int nx[3], int nk);
+cudaError_t launch_diag(const Handle& H, const void* f, int what, int j, double* buf, double* out_dev,
+                        cudaStream_t s);
 // the per-x symbol table (k_xsym.cu), [nxp][N][2N][2N] in the storage type; needs H.d_T
 size_t xs_table_bytes(int nk, int64_t nxp, size_t elt);
 cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s);
@@ -128,6 +133,7 @@ struct Handle {
   double* d_partials = nullptr;
   double* d_result = nullptr;
   double* d_vx = nullptr;          // V(x) per x point (FP64)
+  double* d_diag = nullptr;        // diagnostics: per-x partial sums and the result
   // host-buffer entry point
   void* d_fhost = nullptr;
   // step graph cache

@@ -120,10 +120,10 @@ def test_workspace_bytes_of_the_two_theta_forms(ch):
     assert 4 * f <= w_tab < 5 * f
     assert 2 * f <= w_mod < 4 * f
     assert w_auto == w_tab
-    # 64^3 x 32^3 FP32: a 137 GB table is above the AUTO limit
-    big_tab = ch.workspace_bytes(64, 32, nuclei=nuc, theta_form=ch.THETA_TABLE)
-    assert big_tab >= 4 * 64 ** 3 * 32 ** 3 * 4
-    assert ch.workspace_bytes(64, 32, nuclei=nuc) < big_tab
+    # 128^3 x 32^3 FP32: a 1.1 TB table is above the AUTO limit on any device
+    big_tab = ch.workspace_bytes(128, 32, nuclei=nuc, theta_form=ch.THETA_TABLE)
+    assert big_tab >= 4 * 128 ** 3 * 32 ** 3 * 4
+    assert ch.workspace_bytes(128, 32, nuclei=nuc) < big_tab
     # LPC1 adds two work copies of f to the table form and to the quadratic potential
     assert ch.workspace_bytes(16, 16, nuclei=nuc, theta_form=ch.THETA_TABLE,
                               integrator=ch.LPC1) == w_tab + 2 * f

@@ -127,3 +127,28 @@ def test_lpc1_stability_limit_is_enforced(ch):
         assert e.value.code == ch.chasm.EUNSTABLE
         s.step(f, 0.005, 1)               # within the limit; the handle is still usable
         s.sync()
+
+
+# ------------------------------------------------------------------------------------------------
+# Phase-space diagnostics (Sec. 5)
+@pytest.mark.parametrize("name,nk,nx", [("fp64", 8, (7, 5, 6)), ("fp32", 16, (6, 7, 5)),
+                                        ("fp32", 32, (4, 5, 6))])
+def test_diagnostics_match_oracle_and_are_reproducible(ch, name, nk, nx):
+    prob = O.Problem(nx=nx, nk=nk, x_lo=(-3.0, -2.5, -2.0), x_hi=(2.5, 3.0, 2.0), lk=3.5,
+                     nuclei=[((0.1, 0.2, -0.1), 1.0)])
+    f0 = rough_input(prob, 12)
+    fo = oracle_input(f0, name)
+    tol = 1e-12
+    with solver(ch, prob, name, integrator=ch.STRANG) as s:
+        f = to_dev(f0, name)
+        for j in range(3):
+            w = s.reduced_wigner(f, j)
+            ref = O.reduced_wigner(fo, prob, j)
+            assert np.max(np.abs(w - ref)) <= tol * np.max(np.abs(ref))
+            assert np.array_equal(w, s.reduced_wigner(f, j))
+        p = s.marginal_x12(f)
+        ref = O.marginal_x12(fo, prob)
+        assert np.max(np.abs(p - ref)) <= tol * np.max(np.abs(ref))
+        e = np.array(s.expectations(f))
+        assert np.allclose(e, O.expectations(fo, prob), rtol=0, atol=1e-12)
+        assert np.array_equal(e, np.array(s.expectations(f)))
