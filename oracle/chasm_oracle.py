@@ -189,6 +189,86 @@ def spline_coeffs_1d(phi: np.ndarray, axis: int, h: float, n_nb: int) -> np.ndar
     return np.moveaxis(eta, 0, axis)
 
 
+def pmbc_patch_closures(phi: np.ndarray, h: float, n_nb: int, p: int) -> np.ndarray:
+    """The closure values of p patches along axis 0 of phi (n = N+1 nodes, N = p M), steps (1)-(4)
+    of Sec. 3.1.2: entry b = 0 is phi_L of the first patch and b = p phi_R of the last (Eq. 3.5,
+    global natural ends), entry b = 1..p-1 is phi_R^{(b)} = phi_L^{(b+1)} at the shared node
+    s = b M, c_{0,b} phi(x_s) + sum_{j=1}^{n_nb} (c-_{j,b} phi(x_{s-j}) + c+_{j,b} phi(x_{s+j}))
+    (Eq. 3.4 with the coefficients of the inverse natural matrix, reading A7), taps outside [0, N]
+    dropped.  Shape (p+1,) + phi.shape[1:]."""
+    n = phi.shape[0]
+    N = n - 1
+    M = N // p
+    bt = np.linalg.inv(natural_matrix(n, h))
+    cp, cm = pmbc_end_stencils(n, h, n_nb)
+    J = cp.shape[0]
+    out = np.zeros((p + 1,) + phi.shape[1:])
+    out[0] = np.tensordot(cp, phi[0:J], axes=(0, 0))
+    out[p] = np.tensordot(cm, phi[N - np.arange(J)], axes=(0, 0))
+    for b in range(1, p):
+        sn = b * M
+        # rows of eta_{s-1}, eta_{s+1} are s, s+2; the column of phi_j is j+1
+        def c(j):
+            return (-bt[sn, j + 1] + bt[sn + 2, j + 1]) / (2 * h)
+        acc = c(sn) * phi[sn]
+        for j in range(1, n_nb + 1):
+            if sn - j >= 0:
+                acc = acc + c(sn - j) * phi[sn - j]
+            if sn + j <= N:
+                acc = acc + c(sn + j) * phi[sn + j]
+        out[b] = acc
+    return out
+
+
+def advect_1d_patches(phi: np.ndarray, axis: int, h: float, n_nb: int, alpha: np.ndarray,
+                      k_axis: int, p: int) -> np.ndarray:
+    """A along one axis with p patches (Sec. 3.1.2): closures from pmbc_patch_closures, each patch
+    solves its own Hermite-closed system of M+3 unknowns (step (5)), and the value at node j is
+    the local spline of the patch that contains the foot x_j - alpha h (interpolation and
+    correction of Sec. 3.1.3: at an exact shared node the left patch, feet beyond the ends use
+    the end patches, reading A10); local coefficients outside [-1, M+1] are zero."""
+    phi = np.moveaxis(np.asarray(phi, dtype=np.float64), (axis, k_axis), (0, 1))
+    n = phi.shape[0]
+    N = n - 1
+    M = N // p
+    cl = pmbc_patch_closures(phi, h, n_nb, p)
+    A = hermite_matrix(M + 1, h)
+    etas = []
+    for l in range(p):
+        rhs = np.concatenate([cl[l][None], phi[l * M:(l + 1) * M + 1], cl[l + 1][None]])
+        etas.append(np.linalg.solve(A, rhs.reshape(M + 3, -1)).reshape((M + 3,) + phi.shape[1:]))
+    out = np.zeros_like(phi)
+    for kk, a in enumerate(np.asarray(alpha, dtype=np.float64)):
+        for j in range(n):
+            t = j - a                                   # foot in units of h from x_0
+            l = min(max(int(math.ceil(t / M)) - 1, 0), p - 1)
+            tl = t - l * M
+            base = math.floor(tl)
+            for nu in range(int(base) - 1, int(base) + 3):
+                if -1 <= nu <= M + 1:
+                    out[j, kk] += etas[l][nu + 1, kk] * bspline(np.array(tl - nu))
+    return np.moveaxis(out, (0, 1), (axis, k_axis))
+
+
+def advect_patches(f: np.ndarray, prob: Problem, tau: float, p: tuple) -> np.ndarray:
+    """A(tau) with p[d] patches per x-dimension: the 1-D patch transform along x1, x2, x3 in turn
+    (the sum-factorised form of Eq. 3.10; the oracle checks this identity at p = 1 against the
+    64-term sum)."""
+    g = np.asarray(f, dtype=np.float64)
+    ks = prob.ks()
+    for d in range(3):
+        alpha = prob.hbar * ks * tau / (prob.m * prob.hs(d))
+        out = np.empty_like(g)
+        for kd in range(prob.nk):
+            sl = [slice(None)] * 6
+            sl[3 + d] = slice(kd, kd + 1)
+            sub = g[tuple(sl)]
+            out[tuple(sl)] = advect_1d_patches(sub, d, prob.hs(d), prob.n_nb, alpha[kd:kd + 1],
+                                               3 + d, p[d])
+        g = out
+    return g
+
+
 def spline_coeffs_3d(f: np.ndarray, prob: Problem) -> np.ndarray:
     """Tensor-product coefficients eta_{nu1 nu2 nu3}(k) by 1-D solves along x1, x2, x3 in turn
     (Eq. 3.9).  Shape (nx1+2, nx2+2, nx3+2, Nk, Nk, Nk)."""
