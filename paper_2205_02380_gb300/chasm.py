@@ -170,7 +170,7 @@ class Solver:
 
     def __init__(self, nx, nk, x_lo, x_hi, lk, nuclei=(), kappa=0.0, center=(0.0, 0.0, 0.0),
                  hbar=1.0, m=1.0, precision=FP32_MIXED, n_nb=20, use_graphs=True, stream=None,
-                 theta_form=THETA_AUTO, integrator=STRANG):
+                 theta_form=THETA_AUTO, integrator=STRANG, patches=(1, 1, 1)):
         L = lib()
         self._tstream = None
         if stream is None:
@@ -195,6 +195,7 @@ class Solver:
         opt.cuda_stream = stream if stream is not None else None
         opt.theta_form = theta_form
         opt.integrator = integrator
+        opt.patches = (C.c_int32 * 3)(*patches)
         self.opt = opt
         h = C.c_void_p()
         _check(L.chasm_create(C.byref(self.grid), C.byref(self.box), C.byref(self.pot), hbar, m,

@@ -74,7 +74,8 @@ std::string validate(const chasm_grid* grid, const chasm_box* box, const chasm_p
       if (opt->patches[d] < 1) return "options: patches must be >= 1";
       if ((grid->nx[d] - 1) % opt->patches[d] != 0)
         return "options: patches[d] must divide nx[d] - 1";
-      if (opt->patches[d] != 1) return "options: only patches = 1 is implemented";
+      if (opt->patches[d] > 1 && (grid->nx[d] - 1) / opt->patches[d] < 2)
+        return "options: patches[d] must leave at least 2 intervals per patch";
     }
     if (opt->theta_form != CHASM_THETA_AUTO && opt->theta_form != CHASM_THETA_TABLE &&
         opt->theta_form != CHASM_THETA_MODULATED)
@@ -248,6 +249,54 @@ int build_spline_plan(Handle* H) {
     rc = upload_real(H, &H->d_lu[d], lu);
     if (rc) return rc;
     H->h_lu[d] = lu;
+    const int P = H->opt.patches[d];
+    if (P > 1) {   // closure windows of the p + 1 patch boundaries and the patch LU factors
+      const int M = N / P, nb = H->opt.n_nb, W = 2 * nb + 1;
+      std::vector<int> need;
+      for (int b = 1; b < P; ++b) {
+        need.push_back(b * M - 1);
+        need.push_back(b * M + 1);
+      }
+      auto r2 = natural_inverse_rows(n, h, need);
+      std::vector<double> win((size_t)(P + 1) * W, 0.0);
+      for (int j = 0; j < J; ++j) {
+        win[nb + j] = cp[j];                        // b = 0: node j
+        win[(size_t)P * W + nb - j] = cm[j];        // b = p: node N - j
+      }
+      for (int b = 1; b < P; ++b)
+        for (int i = 0; i < W; ++i) {
+          const int node = b * M - nb + i;
+          if (node < 0 || node > N) continue;
+          win[(size_t)b * W + i] = (-r2[2 * (b - 1)][node + 1] + r2[2 * (b - 1) + 1][node + 1]) / (2.0 * h);
+        }
+      if (H->fp64) {
+        rc = upload_real(H, &H->d_pclos[d], win);
+      } else {
+        std::vector<double> hl((size_t)(P + 1) * 2 * W);
+        for (int b = 0; b <= P; ++b)
+          for (int i = 0; i < W; ++i) {
+            const double v = win[(size_t)b * W + i];
+            const float hi = (float)v;
+            hl[((size_t)b * 2) * W + i] = hi;
+            hl[((size_t)b * 2 + 1) * W + i] = (float)(v - (double)hi);
+          }
+        rc = upload_real(H, &H->d_pclos[d], hl);
+      }
+      if (rc) return rc;
+      std::vector<double> plu(2 * (size_t)(M + 1));
+      double cprev = 0.0;
+      for (int i = 0; i <= M; ++i) {
+        const double bb = (i == 0 || i == M) ? 2.0 : 4.0;
+        const double aa = (i == 0) ? 0.0 : 1.0;
+        const double c = (i == M) ? 0.0 : 1.0;
+        const double mlt = 1.0 / (bb - aa * cprev);
+        plu[i] = c * mlt;
+        plu[M + 1 + i] = mlt;
+        cprev = plu[i];
+      }
+      rc = upload_real(H, &H->d_plu[d], plu);
+      if (rc) return rc;
+    }
   }
   return CHASM_OK;
 }
@@ -445,7 +494,9 @@ void free_all(Handle* H) {
   if (H->stream) cudaStreamSynchronize(H->stream);
   if (H->graph) cudaGraphExecDestroy(H->graph);
   H->graph = nullptr;
-  void* ptrs[] = {H->d_clos[0], H->d_clos[1], H->d_clos[2], H->d_lu[0], H->d_lu[1], H->d_lu[2], H->adv.dev, H->d_T,
+  void* ptrs[] = {H->d_clos[0], H->d_clos[1], H->d_clos[2], H->d_lu[0], H->d_lu[1], H->d_lu[2],
+                  H->d_pclos[0], H->d_pclos[1], H->d_pclos[2], H->d_plu[0], H->d_plu[1], H->d_plu[2],
+                  H->adv.dev, H->d_T,
                   H->d_that, H->d_phase, H->d_sig, H->d_scratch, H->d_u[0], H->d_u[1], H->d_krows,
                   H->d_partials, H->d_result, H->d_vx, H->d_diag, H->d_fhost};
   for (void* p : ptrs)
@@ -686,7 +737,7 @@ int chasm_create(const chasm_grid* grid, const chasm_box* box, const chasm_poten
     H->own_stream = true;
   }
   for (int d = 0; d < 3; ++d)
-    if ((size_t)(g.nx[d] + 2) * kAdvectThreads * H->elt > (size_t)kAdvectMaxSmem) {
+    if (advect_smem_elems(g.nx[d], o.patches[d]) * kAdvectThreads * H->elt > (size_t)kAdvectMaxSmem) {
       std::string m = "nx[d] too large for the advection kernel's shared-memory line buffer";
       if (H->own_stream) cudaStreamDestroy(H->stream);
       delete H;

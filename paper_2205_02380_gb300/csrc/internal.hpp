@@ -43,6 +43,12 @@ struct Handle;
 // advection (k_advect.cu)
 constexpr int kAdvectThreads = 128;
 constexpr int kAdvectMaxSmem = 200 * 1024;
+// shared-memory elements per line of the general advection kernel: the line (n + 2), and for
+// p > 1 patches the line, the p + 1 closure values (hi and lo parts) and the p (M + 3) patch
+// coefficients
+inline size_t advect_smem_elems(int n, int p) {
+  return p > 1 ? (size_t)n + 2 * (p + 1) + (size_t)p * ((n - 1) / p + 3) : (size_t)n + 2;
+}
 cudaError_t advect_prepare();
 cudaError_t launch_advect_dim(const Handle& H, void* f, int dim, cudaStream_t s);
 // Coulomb operator (k_theta.cu): out = (base or 0) + sum_a coef[a] * Theta_a[in]
@@ -110,6 +116,10 @@ struct Handle {
   // [c+ hi | c+ lo | c- hi | c- lo] (unevaluated float pairs for the compensated dot product)
   void* d_clos[3] = {nullptr, nullptr, nullptr};
   void* d_lu[3] = {nullptr, nullptr, nullptr};   // [cprime (n) | mult (n)] in storage type
+  // patches p > 1 (Sec. 3.1.2): closure windows [(p+1)][W] (FP32: [(p+1)][2][W] hi/lo) for the
+  // nodes b M - n_nb + i, W = 2 n_nb + 1, and the LU factors of the (M+1)-node patch system
+  void* d_pclos[3] = {nullptr, nullptr, nullptr};
+  void* d_plu[3] = {nullptr, nullptr, nullptr};
   // host copies (FP64) of the closure stencils [c+ (n) | c- (n)] and LU factors [cprime | mult],
   // passed by value to the register advection kernel
   std::vector<double> h_clos[3], h_lu[3];

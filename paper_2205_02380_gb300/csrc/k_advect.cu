@@ -292,6 +292,108 @@ __global__ void __launch_bounds__(kAdvectThreads) k_advect_smem(AdvParams<T> p) 
   }
 }
 
+// ---- patches (p > 1): Sec. 3.1.2 steps (1)-(5) and the interpolation with correction of
+// Sec. 3.1.3, one line per thread in shared memory (column layout) ----
+template <typename T>
+struct PatchArgs {
+  int P, M, nb, W;
+  const T* win;   // closure windows: FP64 [(P+1)][W]; FP32 [(P+1)][2][W] (hi, lo)
+  const T* lu;    // [c' (M+1) | 1/pivot (M+1)] of the (M+1)-node patch system
+};
+
+// closure value of boundary b = sum over its window of coefficient * phi, hi/lo parts
+__device__ __forceinline__ void patch_closure(const PatchArgs<double>& q, const double* buf, int B, int N,
+                                              int b, double& hi, double& lo) {
+  double acc = 0.0;
+  for (int i = 0; i < q.W; ++i) {
+    const int node = b * q.M - q.nb + i;
+    if (node >= 0 && node <= N) acc = fma(__ldg(q.win + (size_t)b * q.W + i), buf[(size_t)node * B], acc);
+  }
+  hi = acc;
+  lo = 0.0;
+}
+__device__ __forceinline__ void patch_closure(const PatchArgs<float>& q, const float* buf, int B, int N,
+                                              int b, float& hi, float& lo) {
+  DF acc{0.f, 0.f};
+  const float* w = q.win + (size_t)b * 2 * q.W;
+  for (int i = 0; i < q.W; ++i) {
+    const int node = b * q.M - q.nb + i;
+    if (node >= 0 && node <= N) df_acc(acc, buf[(size_t)node * B], __ldg(w + i), __ldg(w + q.W + i));
+  }
+  hi = acc.hi;
+  lo = acc.lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAdvectThreads) k_advect_patches(AdvParams<T> p, PatchArgs<T> q) {
+  extern __shared__ unsigned char smem_raw[];
+  const int B = blockDim.x;
+  const int n = p.n, N = n - 1, P = q.P, M = q.M;
+  T* buf = reinterpret_cast<T*>(smem_raw) + threadIdx.x;   // phi_j at buf[j B]
+  T* cvh = buf + (size_t)n * B;                             // closure b: cvh[b B], cvl[b B]
+  T* cvl = cvh + (size_t)(P + 1) * B;
+  T* eta = cvl + (size_t)(P + 1) * B;                       // eta^(l)_nu at eta[(l (M+3) + nu + 1) B]
+  const int64_t line = (int64_t)blockIdx.x * B + threadIdx.x;
+  if (line >= p.n_lines) return;
+  T* src;
+  int kd;
+  line_setup(p, line, src, kd);
+  for (int j = 0; j < n; ++j) buf[(size_t)j * B] = src[(int64_t)j * p.s_d];
+  for (int b = 0; b <= P; ++b) {
+    T hi, lo;
+    patch_closure(q, buf, B, N, b, hi, lo);
+    cvh[(size_t)b * B] = hi;
+    cvl[(size_t)b * B] = lo;
+  }
+  const T* cprime = q.lu;
+  const T* mult = q.lu + (M + 1);
+  for (int l = 0; l < P; ++l) {
+    const T* ph = buf + (size_t)l * M * B;
+    T* e = eta + (size_t)l * (M + 3) * B;
+    Closure<T> cl;   // phi_L of patch l in cl.L, phi_R in cl.R
+    if constexpr (sizeof(T) == 4) {
+      cl.L = DF{cvh[(size_t)l * B], cvl[(size_t)l * B]};
+      cl.R = DF{cvh[(size_t)(l + 1) * B], cvl[(size_t)(l + 1) * B]};
+    } else {
+      cl.L = cvh[(size_t)l * B];
+      cl.R = cvh[(size_t)(l + 1) * B];
+    }
+    T dp = (T)cl.d0(ph[0], hval(p)) * __ldg(mult);
+    e[B] = dp;
+    for (int i = 1; i < M; ++i) {
+      dp = ((T)6 * ph[(size_t)i * B] - dp) * __ldg(mult + i);
+      e[(size_t)(i + 1) * B] = dp;
+    }
+    dp = ((T)cl.dN(ph[(size_t)M * B], hval(p)) - dp) * __ldg(mult + M);
+    e[(size_t)(M + 1) * B] = dp;
+    T nx = dp;
+    for (int i = M - 1; i >= 0; --i) {
+      nx = e[(size_t)(i + 1) * B] - __ldg(cprime + i) * nx;
+      e[(size_t)(i + 1) * B] = nx;
+    }
+    e[0] = (T)cl.gl(e[2 * (size_t)B], h2val(p));
+    e[(size_t)(M + 2) * B] = (T)cl.gr(e[(size_t)M * B], h2val(p));
+  }
+  const int sh = __ldg(p.ns + kd);
+  const T w[4] = {__ldg(p.w + 4 * kd + 0), __ldg(p.w + 4 * kd + 1), __ldg(p.w + 4 * kd + 2),
+                  __ldg(p.w + 4 * kd + 3)};
+  for (int j = 0; j < n; ++j) {
+    // patch of the foot x_j - (sh + a) h: floor((j - sh - 1) / M), clamped (left patch at a node)
+    const int t = j - sh - 1;
+    int l = t >= 0 ? t / M : -((-t + M - 1) / M);
+    l = l < 0 ? 0 : (l > P - 1 ? P - 1 : l);
+    const int nu0 = j - l * M - sh - 2;   // first tap, local index
+    const T* e = eta + (size_t)l * (M + 3) * B;
+    T acc = (T)0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int nu = nu0 + c;
+      if (nu >= -1 && nu <= M + 1) acc = fma(w[c], e[(size_t)(nu + 1) * B], acc);
+    }
+    src[(int64_t)j * p.s_d] = acc;
+  }
+}
+
 template <typename T>
 cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
   const GridDesc& g = H.g;
@@ -321,6 +423,19 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
   p.ns = reinterpret_cast<const int*>(wbase + (size_t)3 * g.nk * 4) + dim * g.nk;
   const int B = kAdvectThreads;
   const unsigned blocks = (unsigned)((p.n_lines + B - 1) / B);
+  const int P = H.opt.patches[dim];
+  if (P > 1) {
+    PatchArgs<T> q;
+    q.P = P;
+    q.M = (p.n - 1) / P;
+    q.nb = H.opt.n_nb;
+    q.W = 2 * q.nb + 1;
+    q.win = static_cast<const T*>(H.d_pclos[dim]);
+    q.lu = static_cast<const T*>(H.d_plu[dim]);
+    const size_t smem = advect_smem_elems(p.n, P) * B * sizeof(T);
+    k_advect_patches<T><<<blocks, B, smem, s>>>(p, q);
+    return cudaGetLastError();
+  }
   const bool reg_shift = H.adv.ns_min[dim] >= -2 && H.adv.ns_max[dim] <= 1;
   if (reg_shift && p.n <= kRegMaxNx) {
     const int64_t lpt = sizeof(T) == 4 ? 2 : 1;   // kvol = nk^3 is even
@@ -374,8 +489,13 @@ cudaError_t advect_prepare() {
   cudaError_t e = cudaFuncSetAttribute(k_advect_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kAdvectMaxSmem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_advect_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kAdvectMaxSmem);
+  e = cudaFuncSetAttribute(k_advect_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kAdvectMaxSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_advect_patches<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdvectMaxSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_advect_patches<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdvectMaxSmem);
+  return e;
 }
 
 cudaError_t launch_advect_dim(const Handle& H, void* f, int dim, cudaStream_t s) {

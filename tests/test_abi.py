@@ -88,6 +88,7 @@ def _create(ch, nx=(8, 8, 8), nk=16, lo=-4.0, hi=4.0, lk=4.0, nuclei=(), hbar=1.
     (dict(n_nb=0), "n_nb"),
     (dict(patches=(2, 1, 1), nx=(8, 8, 8)), "divide"),
     (dict(patches=(7, 1, 1), nx=(8, 8, 8)), "patches"),
+    (dict(patches=(1, 4, 1), nx=(8, 5, 8)), "intervals per patch"),
     (dict(nuclei=[((float("nan"), 0, 0), 1.0)]), "nucleus"),
     (dict(theta_form=3), "theta_form"),
     (dict(integrator=2), "integrator"),
