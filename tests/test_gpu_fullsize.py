@@ -118,3 +118,22 @@ def test_fullsize_mixed_form_tracks_fp64_over_steps(ch):
     diff = torch.linalg.vector_norm(out["fp32"] - out["fp64"]) / torch.linalg.vector_norm(out["fp64"])
     assert float(diff) <= 1e-5, float(diff)
     assert abs(mass["fp32"] - mass["fp64"]) <= 1e-6 * abs(mass["fp64"])
+
+
+def test_fullsize_lpc1_mixed_form_tracks_fp64(ch):
+    """The LPC1 integrator at the full size (the bench's lpc1 section): FP32-mixed against FP64
+    over two steps (LPC1's FP64 form is pinned to the oracle in test_gpu_lpc1.py)."""
+    out = {}
+    mass = {}
+    for name in ("fp64", "fp32"):
+        with ch.Solver(NX, NK, -L, L, LK, nuclei=NUC, integrator=ch.LPC1,
+                       precision=ch.FP64 if name == "fp64" else ch.FP32_MIXED) as s:
+            f = device_input(name)
+            s.step(f, DT, 2)
+            s.sync()
+            mass[name] = s.mass(f)
+            out[name] = f.double()
+            del f
+    diff = torch.linalg.vector_norm(out["fp32"] - out["fp64"]) / torch.linalg.vector_norm(out["fp64"])
+    assert float(diff) <= 1e-5, float(diff)
+    assert abs(mass["fp32"] - mass["fp64"]) <= 1e-6 * abs(mass["fp64"])
