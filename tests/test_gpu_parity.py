@@ -314,3 +314,35 @@ def test_table_and_modulated_forms_agree(ch):
             s.sync()
             outs.append(f.cpu().numpy())
     assert O.rel_l2(outs[0], outs[1]) <= 1e-13
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_nucleus_on_a_grid_node(ch, form):
+    """Degenerate x point: at x = x_A the modulation is 1 (the per-x kernel sin(2 (x - x_A).m dk)
+    vanishes), so Theta^T is zero there up to rounding; elsewhere it matches the oracle."""
+    prob = problem((5, 5, 5), 16, -2.0, 2.0, 4.0, nuclei=[((0.0, 1.0, -1.0), 1.0)])
+    f0 = rough_input(prob, 41)
+    with solver(ch, prob, "fp64", form) as s:
+        u = to_dev(f0, "fp64")
+        out = torch.empty_like(u)
+        s.theta(u, out)
+        s.sync()
+        got = out.cpu().numpy()
+    assert np.max(np.abs(got[2, 3, 1])) <= 1e-13 * np.max(np.abs(got))   # x_A is node (2, 3, 1)
+    ref = O.theta_coulomb(f0, prob)
+    assert O.rel_l2(got, ref) <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("name", ["fp64", "fp32"])
+def test_zero_data_and_zero_steps(ch, name):
+    prob = problem((6, 5, 4), 8, -3.0, 3.0, 3.0, nuclei=[((0.1, 0.0, 0.2), 1.0)])
+    f0 = rough_input(prob, 43)
+    with solver(ch, prob, name) as s:
+        z = torch.zeros(prob.shape, device="cuda", dtype=dtype(name))
+        s.step(z, 0.02, 2)
+        f = to_dev(f0, name)
+        before = f.clone()
+        s.step(f, 0.02, 0)
+        s.sync()
+        assert int(torch.count_nonzero(z)) == 0
+        assert torch.equal(f, before)
