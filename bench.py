@@ -348,9 +348,9 @@ def run_chasm(args):
             ms_t, value = aggregate_ranks(ms, cells, steps, dist, "cuda")
             entry = {"ms_per_step": ms_t / steps, "steps": steps, "value": value,
                      "mass0": m0, "mass": m1, "energy0": e0, "energy": e1}
+            entry["pflow_ms"] = time_pflow_launches(torch, s, f, dt, stream,
+                                                    5 if prec_name == "fp32" else 1)
             if prec_name == "fp32":
-                reps = 5
-                entry["pflow_ms"] = time_pflow_launches(torch, s, f, dt, stream, reps)
                 # end-to-end through the C ABI with HOST buffers (pinned), copies included
                 host = torch.empty(f.shape, dtype=dtp, pin_memory=True)
                 host.copy_(f.cpu())
@@ -396,7 +396,12 @@ def run_chasm(args):
     nk = W["nk"]
     flops_launch = 4 * theta_flops_per_cell(nk) * cells
     achieved = flops_launch / (r32["pflow_ms"] / 1e3) / 1e12
+    achieved64 = flops_launch / (r64["pflow_ms"] / 1e3) / 1e12
     peak = fp32_alu_peak_tflops()
+    try:
+        fma32, fma64 = ch.chasm.fma_peaks()
+    except Exception:
+        fma32 = fma64 = None
     tr = committed_traffic()
     line = {
         "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
@@ -407,7 +412,8 @@ def run_chasm(args):
                    "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (f = %.1f GB)" % (cells * 4 / 1e9)},
         "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
-                 "dtype": "f64"},
+                 "dtype": "f64", "pflow_ms": r64["pflow_ms"], "pflow_tflops": achieved64,
+                 "pflow_frac_of_measured_fp64_fma": (achieved64 / fma64) if fma64 else None},
         "accuracy": accuracy,
         "lpc1": lpc1,
         "serving": serving,
@@ -416,6 +422,8 @@ def run_chasm(args):
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "measured_fma_peak_tflops": fma32,
+                     "frac_of_measured_fma_peak": (achieved / fma32) if fma32 else None,
                      "ms_per_launch": r32["pflow_ms"],
                      "flops_per_launch": flops_launch,
                      "traffic": (tr["dram_bytes_per_launch"] * cells / tr["cells"]) if tr else None},

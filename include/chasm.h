@@ -205,6 +205,13 @@ int chasm_reduced_wigner(chasm_handle* h, const void* f_dev, int32_t j, double* 
 int chasm_marginal_x12(chasm_handle* h, const void* f_dev, double* p_host);
 int chasm_expectations(chasm_handle* h, const void* f_dev, double* out_host);
 
+/* Measures the SIMT fused-multiply-add throughput of the current device (independent FMA chains on
+ * every SM, two flops per FMA), in TFLOP/s, FP32 and FP64: the ALU ceiling of the Coulomb kernels,
+ * which are bound by plain FMA/add arithmetic.  Either pointer may be NULL (not both).  Allocates
+ * and frees a small device buffer; synchronous, about a second.  Not part of the paper: a
+ * measurement utility for roofline reports. */
+int chasm_fma_peaks(double* fp32_tflops, double* fp64_tflops);
+
 /* Mass and energy exactly as chasm_moments defines them, for callers that cannot allocate
  * device memory when they need them: code running while a stream is captured in the global
  * capture mode (cudaMalloc is not allowed then), services that reserve their whole memory budget

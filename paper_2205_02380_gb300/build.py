@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchasm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "k_advect.cu", "k_theta.cu", "k_theta_xs.cu", "k_xsym.cu", "k_symbol.cu",
-           "k_misc.cu", "k_lpc1.cu", "k_diag.cu", "server.cu", "noalloc.cu"]
+           "k_misc.cu", "k_lpc1.cu", "k_diag.cu", "k_peak.cu", "server.cu",
+           "noalloc.cu"]
 
 
 def nvcc() -> str:

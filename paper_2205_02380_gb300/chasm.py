@@ -91,6 +91,7 @@ _SIGS = [
     ("chasm_reduced_wigner", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_double)]),
     ("chasm_marginal_x12", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("chasm_expectations", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    ("chasm_fma_peaks", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("chasm_moments_noalloc", C.c_int, [C.c_void_p, C.POINTER(Grid), C.POINTER(Box), C.POINTER(Potential),
                                         C.c_double, C.c_double, C.c_int32, C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -397,3 +398,10 @@ def make_request(nx, nk, x_lo, x_hi, lk, dt, nsteps, nuclei=(), kappa=0.0, packe
     r.f0_host = f0_ptr
     r.f_out_host = fout_ptr
     return r
+
+
+def fma_peaks():
+    """(FP32, FP64) SIMT FMA throughput of the current device in TFLOP/s (chasm_fma_peaks)."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib().chasm_fma_peaks(C.byref(a), C.byref(b)))
+    return a.value, b.value

@@ -952,6 +952,14 @@ int chasm_expectations(chasm_handle* h, const void* f, double* out_host) {
   return diag_call(h, f, 2, 0, out_host, 6);
 }
 
+int chasm_fma_peaks(double* fp32_tflops, double* fp64_tflops) {
+  if (!fp32_tflops && !fp64_tflops) return fail(nullptr, CHASM_EINVAL, "both outputs are NULL");
+  const cudaError_t e = measure_fma_peaks(fp32_tflops, fp64_tflops);
+  if (e != cudaSuccess)
+    return fail(nullptr, CHASM_ECUDA, std::string("chasm_fma_peaks: ") + cudaGetErrorString(e));
+  return CHASM_OK;
+}
+
 int chasm_mass(chasm_handle* h, const void* f, double* out) {
   if (!out) return fail(reinterpret_cast<Handle*>(h), CHASM_EINVAL, "out is NULL");
   return chasm_moments(h, f, out, nullptr);

@@ -1,0 +1,70 @@
+// SIMT fused-multiply-add throughput of the current device, FP32 and FP64, for the ALU roofline
+// of the Coulomb kernels (which are bound by plain FMA/add arithmetic, not by HBM or tensor cores).
+// Every thread runs K independent FMA chains (enough independent work to hide the pipeline
+// latency) for `iters` rounds; the grid covers every SM several times over.  Counted flops: two
+// per FMA.  The chains' final values are written out so the compiler keeps the work.
+#include "internal.hpp"
+
+namespace chasm {
+namespace {
+
+constexpr int kChains = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T* __restrict__ out, int iters, T a, T b) {
+  T v[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) v[c] = (T)(threadIdx.x + c) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) v[c] = fma(v[c], a, b);
+    }
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += v[c];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+cudaError_t measure(int num_sms, int iters, double* tflops) {
+  const int blocks = num_sms * 8, threads = 256;
+  T* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc((void**)&out, (size_t)blocks * threads * sizeof(T));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    // a = 1 - 2^-20, b = 2^-20: the chains stay bounded
+    const T a = (T)(1.0 - 1.0 / 1048576.0), b = (T)(1.0 / 1048576.0);
+    k_fma_peak<T><<<blocks, threads>>>(out, iters / 4, a, b);   // warm-up
+    e = cudaEventRecord(e0);
+    k_fma_peak<T><<<blocks, threads>>>(out, iters, a, b);
+    if (e == cudaSuccess) e = cudaEventRecord(e1);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && ms > 0.f)
+      *tflops = 2.0 * kChains * 16.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (out) cudaFree(out);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t measure_fma_peaks(double* fp32_tflops, double* fp64_tflops) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess && fp32_tflops) e = measure<float>(sms, 256, fp32_tflops);
+  if (e == cudaSuccess && fp64_tflops) e = measure<double>(sms, 8, fp64_tflops);
+  return e;
+}
+
+}  // namespace chasm
