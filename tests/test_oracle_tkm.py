@@ -177,3 +177,29 @@ def test_coulomb_pflow_is_the_fourth_order_taylor_polynomial():
     e1 = np.max(np.abs(O.pflow_coulomb(f, prob, 0.1).reshape(-1) - expm(0.1 * M) @ v))
     e2 = np.max(np.abs(O.pflow_coulomb(f, prob, 0.05).reshape(-1) - expm(0.05 * M) @ v))
     assert e1 / e2 > 20.0   # ~2^5
+
+
+def test_theta_approaches_the_classical_force_term_far_from_the_nucleus():
+    """Classical limit: far from the nucleus Theta^T[f] -> (1/hbar) grad V . grad_k f with
+    V = -Z/|x| (the sign of Eq. 2.3; Eq. 5.1 for the quadratic case), the first quantum correction
+    (hbar^2/24) d^3V d^3_k f being O(|x|^-2) relative.  The relative deviation times |x|^2 stays
+    constant while it falls 16-fold from |x| = 2 to 8 (a wrong sign leaves it near 2, a wrong
+    prefactor leaves a constant).  The k-grid must resolve the modulation: 2 |x| dk < pi."""
+    nk, lk = 32, 3.0
+    prob = O.Problem(nx=(1, 1, 1), nk=nk, x_lo=(0.0,) * 3, x_hi=(1.0,) * 3, lk=lk,
+                     nuclei=[((0.0, 0.0, 0.0), 1.0)])
+    ks = prob.ks()
+    K = np.stack(np.meshgrid(ks, ks, ks, indexing="ij"), -1)
+    b, k0 = 2.0, np.array([0.3, -0.2, 0.1])
+    f = np.exp(-b * np.sum((K - k0) ** 2, -1))
+    grad = -2 * b * (K - k0) * f[..., None]
+    T = O.tkm_tensor(nk, lk)
+    scaled = []
+    for r in (2.0, 4.0, 8.0):
+        x = np.array([[0.6 * r, 0.8 * r, 0.0]])
+        th = O.theta_coulomb(f[None], prob, T, xpts=x)[0]
+        classical = np.tensordot(grad, x[0] / np.linalg.norm(x[0]) ** 3, axes=([3], [0]))
+        e = np.linalg.norm(th - classical) / np.linalg.norm(classical)
+        scaled.append(e * r * r)
+    assert e < 0.05
+    assert max(scaled) / min(scaled) < 1.3, scaled
