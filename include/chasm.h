@@ -76,7 +76,8 @@ enum { CHASM_THETA_AUTO = 0, CHASM_THETA_TABLE = 1, CHASM_THETA_MODULATED = 2 };
  *     g(A_dt(x, k)) = g(x - hbar k dt / m, k) evaluated by the advection of Sec. 3 (one
  *     advection of f and one of Theta_V[f] per step) and Theta_V applied twice per step; for the
  *     quadratic potential Theta_V f = kappa (x - c)/hbar . grad_k f with the spectral k-derivative.
- *     Needs two more copies of f of workspace (the modulated Coulomb form already has them).
+ *     Needs more workspace: one copy of f in the table form (the predictor is formed inside the
+ *     Theta kernel), two for the quadratic potential; the modulated Coulomb form already has them.
  *     EUNSTABLE when dt rho > 1, rho the spectral-radius bound of Theta_V (chasm_step below). */
 enum { CHASM_STRANG = 0, CHASM_LPC1 = 1 };
 

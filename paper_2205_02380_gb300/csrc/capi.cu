@@ -573,8 +573,9 @@ int theta_any(Handle* H, const void* in, const void* base, void* out, double c) 
   return CHASM_OK;
 }
 
-// One LPC1 step (Sec. 2.2): U = Theta f; advect f (= g) and U (= h) by dt; V = g + dt h (the
-// predictor), f = g + dt/2 h; f += dt/2 Theta V.
+// One LPC1 step (Sec. 2.2): U = Theta f; advect f (= g) and U (= h) by dt; then
+// f = (g + dt/2 h) + dt/2 Theta[g + dt h].  The table form forms the predictor g + dt h and the
+// corrector base in the Theta kernel itself; the other forms go through V = g + dt h.
 int issue_step_lpc1(Handle* H, void* f, double dt) {
   void* U = H->d_u[0];
   void* V = H->d_u[1];
@@ -584,6 +585,16 @@ int issue_step_lpc1(Handle* H, void* f, double dt) {
   if (rc) return rc;
   rc = do_advect(H, U, dt, true);
   if (rc) return rc;
+  if (!H->nuclei.empty() && H->xs) {
+    XsExtra x;
+    x.in2 = U;
+    x.cin2 = dt;
+    x.base2 = U;
+    x.cbase2 = 0.5 * dt;
+    const double c = 0.5 * dt;
+    CHASM_CUDA(H, launch_theta_xs(*H, f, f, f, 1, &c, H->stream, x));
+    return CHASM_OK;
+  }
   CHASM_CUDA(H, launch_lpc1_combine(*H, f, U, V, dt, H->stream));
   return theta_any(H, V, f, f, 0.5 * dt);
 }
@@ -668,7 +679,7 @@ size_t chasm_workspace_bytes(const chasm_grid* grid, const chasm_potential* pot,
     }
     w += tp.scratch_bytes;
     w += (size_t)8 * nk * nk * nk * e + (size_t)(2 * nk - 1) * (2 * nk - 1) * (2 * nk - 1) * 8;
-    if (xs && o.integrator == CHASM_LPC1) w += 2 * fbytes;
+    if (xs && o.integrator == CHASM_LPC1) w += fbytes;   // Theta f (the predictor is formed in-kernel)
   } else if (o.integrator == CHASM_LPC1) {
     w += 2 * fbytes;
   }
@@ -783,9 +794,10 @@ int chasm_create(const chasm_grid* grid, const chasm_box* box, const chasm_poten
         return bail(fail(H, CHASM_ENOMEM, "device allocation failed (Horner buffers / scratch)"));
     }
   }
-  if (o.integrator == CHASM_LPC1 && !H->d_u[0]) {   // the two LPC1 work copies of f
+  if (o.integrator == CHASM_LPC1 && !H->d_u[0]) {   // LPC1 work copies: Theta f, the predictor
+    const bool fused = !H->nuclei.empty() && H->xs;  // the table form forms the predictor in-kernel
     if (cudaMallocAsync(&H->d_u[0], fbytes, H->stream) != cudaSuccess ||
-        cudaMallocAsync(&H->d_u[1], fbytes, H->stream) != cudaSuccess)
+        (!fused && cudaMallocAsync(&H->d_u[1], fbytes, H->stream) != cudaSuccess))
       return bail(fail(H, CHASM_ENOMEM, "device allocation failed (LPC1 buffers)"));
   }
   e = cudaStreamSynchronize(H->stream);

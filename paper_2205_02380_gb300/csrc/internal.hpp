@@ -60,10 +60,16 @@ struct ThetaPlan {
   size_t scratch_bytes = 0; // global scratch of the fallback kernel
 };
 void theta_plan(int nk, bool fp64, int64_t nxp, int num_sms, ThetaPlan* plan);
-// real form with the per-x symbol table (k_theta_xs.cu): u_0 = in, u_{s+1} = (base or 0) +
-// coef[s] Theta^T[u_s] for s < nst (1..4), out = u_nst; out may alias in and base
+// real form with the per-x symbol table (k_theta_xs.cu): u_0 = in + cin2 in2, u_{s+1} =
+// (base + cbase2 base2, or 0) + coef[s] Theta^T[u_s] for s < nst (1..4), out = u_nst; out may
+// alias in, in2, base and base2 (in2, base2 null: the plain forms)
+struct XsExtra {
+  const void* in2 = nullptr;
+  const void* base2 = nullptr;
+  double cin2 = 0.0, cbase2 = 0.0;
+};
 cudaError_t launch_theta_xs(const Handle& H, const void* in, const void* base, void* out, int nst,
-                            const double* coef, cudaStream_t s);
+                            const double* coef, cudaStream_t s, const XsExtra& x = XsExtra());
 void theta_xs_plan(int nk, bool fp64, int64_t nxp, int num_sms, ThetaPlan* plan);
 // LPC1 (k_lpc1.cu): Theta of the quadratic potential, out = (base or 0) + coef Theta[in]
 // (in must not alias out), and the predictor/corrector combination v = f + dt h, f = f + dt/2 h

@@ -36,9 +36,12 @@ namespace {
 
 template <typename T>
 struct XsParams {
-  const T* in;     // stage-0 input u_0
-  const T* base;   // Horner base (f) or null (out = c Theta)
-  T* out;          // result of the last stage; may alias in and base
+  const T* in;     // stage-0 input u_0 = in + cin2 in2 (in2 may be null)
+  const T* base;   // Horner base base + cbase2 base2 (base2 may be null), or null (out = c Theta)
+  const T* in2;
+  const T* base2;
+  T cin2, cbase2;
+  T* out;          // result of the last stage; may alias in, in2, base and base2
   int64_t nxp;
   const T* sig;    // [nxp][N][2N][2N] symbol table
   int nst;         // stages, 1..4
@@ -100,14 +103,21 @@ __device__ __forceinline__ void load_col(const cpx<T>* g, int stride, T (&re)[N]
   }
 }
 
-// re[n] <- b[n] + c Re[e^{+i pi n/(2N)} (re[n] + i im[n])]   (b null: 0)
+// re[n] <- (b[n] + cb2 b2[n]) + c Re[e^{+i pi n/(2N)} (re[n] + i im[n])]   (b null: 0; b2 null: b)
 template <typename T, int N>
-__device__ __forceinline__ void horner_line(T (&re)[N], const T (&im)[N], const T* b, T c) {
+__device__ __forceinline__ void horner_line(T (&re)[N], const T (&im)[N], const T* b, const T* b2,
+                                            T cb2, T c) {
   if constexpr (sizeof(T) == 4 && N % 4 == 0) {
     const float4* b4 = reinterpret_cast<const float4*>(b);
+    const float4* c4 = reinterpret_cast<const float4*>(b2);
 #pragma unroll
     for (int q = 0; q < N / 4; ++q) {
-      const float4 bb = b ? b4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 bb = b ? b4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (b2) {
+        const float4 cc = c4[q];
+        bb = make_float4(fmaf(cb2, cc.x, bb.x), fmaf(cb2, cc.y, bb.y), fmaf(cb2, cc.z, bb.z),
+                         fmaf(cb2, cc.w, bb.w));
+      }
       const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -117,10 +127,15 @@ __device__ __forceinline__ void horner_line(T (&re)[N], const T (&im)[N], const 
       }
     }
   } else {
-    const double2* b2 = reinterpret_cast<const double2*>(b);
+    const double2* bd = reinterpret_cast<const double2*>(b);
+    const double2* cd = reinterpret_cast<const double2*>(b2);
 #pragma unroll
     for (int q = 0; q < N / 2; ++q) {
-      const double2 bb = b ? b2[q] : make_double2(0.0, 0.0);
+      double2 bb = b ? bd[q] : make_double2(0.0, 0.0);
+      if (b2) {
+        const double2 cc = cd[q];
+        bb = make_double2(fma((double)cb2, cc.x, bb.x), fma((double)cb2, cc.y, bb.y));
+      }
       const T bv[2] = {(T)bb.x, (T)bb.y};
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -173,7 +188,9 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
-template <typename T, int N, int NT, bool GSM, int MINB>
+// X2: the second input and base terms (in2, base2) are read (the LPC1 corrector); without it
+// they are compiled out
+template <typename T, int N, int NT, bool GSM, int MINB, bool X2>
 __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
   using C = XsCfg<T, N>;
   constexpr int L = C::L, GS = C::GS, NG = C::NG, SR = C::SR, SLAB = C::SLAB;
@@ -192,6 +209,11 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
       const int off = (line / N) * SR + (line % N);
       T re[N], im[N];
       load_line_plain<T, N>(p.in + xp * N3 + (size_t)line * N, re);
+      if (X2 && p.in2) {   // u_0 = in + cin2 in2 (the LPC1 predictor)
+        load_line_plain<T, N>(p.in2 + xp * N3 + (size_t)line * N, im);
+#pragma unroll
+        for (int n = 0; n < N; ++n) re[n] = fma(p.cin2, im[n], re[n]);
+      }
       twist_real<T, N>(re, im);
       fft<T, N, false>(re, im);
       store_col<T, N, GSM>(G + off, SLAB, re, im, pol);
@@ -223,7 +245,8 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
         T re[N], im[N];
         load_col<T, N, GSM>(G + off, SLAB, re, im, pol);
         fft<T, N, true>(re, im);
-        horner_line<T, N>(re, im, p.base ? p.base + xp * N3 + (size_t)line * N : nullptr, c);
+        horner_line<T, N>(re, im, p.base ? p.base + xp * N3 + (size_t)line * N : nullptr,
+                          X2 && p.base2 ? p.base2 + xp * N3 + (size_t)line * N : nullptr, p.cbase2, c);
         if (last) {
           store_line_cs<T, N>(p.out + xp * N3 + (size_t)line * N, re);
         } else {
@@ -237,10 +260,10 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
   }
 }
 
-template <typename T, int N>
+template <typename T, int N, bool X2 = false>
 auto xs_kernel() {
   using C = XsCfg<T, N>;
-  return k_theta_xs<T, N, C::NT, C::GSM, C::MINB>;
+  return k_theta_xs<T, N, C::NT, C::GSM, C::MINB, X2>;
 }
 
 template <typename T, int N>
@@ -248,6 +271,8 @@ void plan_xs_tn(int64_t nxp, int num_sms, ThetaPlan* pl) {
   using C = XsCfg<T, N>;
   auto kern = xs_kernel<T, N>();
   int nb = 0;
+  cudaFuncSetAttribute(xs_kernel<T, N, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)C::smem_bytes);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes) !=
           cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C::NT, C::smem_bytes) != cudaSuccess ||
@@ -260,36 +285,43 @@ void plan_xs_tn(int64_t nxp, int num_sms, ThetaPlan* pl) {
 
 template <typename T, int N>
 cudaError_t launch_xs_tn(const Handle& H, const void* in, const void* base, void* out, int nst,
-                         const double* coef, cudaStream_t s) {
+                         const double* coef, const XsExtra& x, cudaStream_t s) {
   using C = XsCfg<T, N>;
   XsParams<T> p;
   p.in = static_cast<const T*>(in);
   p.base = static_cast<const T*>(base);
+  p.in2 = static_cast<const T*>(x.in2);
+  p.base2 = static_cast<const T*>(x.base2);
+  p.cin2 = (T)x.cin2;
+  p.cbase2 = (T)x.cbase2;
   p.out = static_cast<T*>(out);
   p.nxp = H.g.nxp;
   p.sig = static_cast<const T*>(H.d_sig);
   p.nst = nst;
   for (int q = 0; q < 4; ++q) p.coef[q] = q < nst ? (T)coef[q] : (T)0;
   p.G = static_cast<cpx<T>*>(H.d_scratch);
-  k_theta_xs<T, N, C::NT, C::GSM, C::MINB><<<H.theta.blocks, C::NT, C::smem_bytes, s>>>(p);
+  if (x.in2 || x.base2)
+    k_theta_xs<T, N, C::NT, C::GSM, C::MINB, true><<<H.theta.blocks, C::NT, C::smem_bytes, s>>>(p);
+  else
+    k_theta_xs<T, N, C::NT, C::GSM, C::MINB, false><<<H.theta.blocks, C::NT, C::smem_bytes, s>>>(p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_theta_xs(const Handle& H, const void* in, const void* base, void* out, int nst,
-                            const double* coef, cudaStream_t s) {
+                            const double* coef, cudaStream_t s, const XsExtra& x) {
   if (nst < 1 || nst > 4 || !H.d_sig) return cudaErrorInvalidValue;
   switch (H.g.nk) {
     case 8:
-      return H.fp64 ? launch_xs_tn<double, 8>(H, in, base, out, nst, coef, s)
-                    : launch_xs_tn<float, 8>(H, in, base, out, nst, coef, s);
+      return H.fp64 ? launch_xs_tn<double, 8>(H, in, base, out, nst, coef, x, s)
+                    : launch_xs_tn<float, 8>(H, in, base, out, nst, coef, x, s);
     case 16:
-      return H.fp64 ? launch_xs_tn<double, 16>(H, in, base, out, nst, coef, s)
-                    : launch_xs_tn<float, 16>(H, in, base, out, nst, coef, s);
+      return H.fp64 ? launch_xs_tn<double, 16>(H, in, base, out, nst, coef, x, s)
+                    : launch_xs_tn<float, 16>(H, in, base, out, nst, coef, x, s);
     case 32:
-      return H.fp64 ? launch_xs_tn<double, 32>(H, in, base, out, nst, coef, s)
-                    : launch_xs_tn<float, 32>(H, in, base, out, nst, coef, s);
+      return H.fp64 ? launch_xs_tn<double, 32>(H, in, base, out, nst, coef, x, s)
+                    : launch_xs_tn<float, 32>(H, in, base, out, nst, coef, x, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -125,9 +125,10 @@ def test_workspace_bytes_of_the_two_theta_forms(ch):
     big_tab = ch.workspace_bytes(128, 32, nuclei=nuc, theta_form=ch.THETA_TABLE)
     assert big_tab >= 4 * 128 ** 3 * 32 ** 3 * 4
     assert ch.workspace_bytes(128, 32, nuclei=nuc) < big_tab
-    # LPC1 adds two work copies of f to the table form and to the quadratic potential
+    # LPC1 adds one work copy of f to the table form (Theta f; the predictor is formed inside the
+    # Theta kernel) and two to the quadratic potential
     assert ch.workspace_bytes(16, 16, nuclei=nuc, theta_form=ch.THETA_TABLE,
-                              integrator=ch.LPC1) == w_tab + 2 * f
+                              integrator=ch.LPC1) == w_tab + f
     assert ch.workspace_bytes(16, 16, nuclei=nuc, theta_form=ch.THETA_MODULATED,
                               integrator=ch.LPC1) == w_mod
     w_h = ch.workspace_bytes(16, 16, kappa=1.0)
