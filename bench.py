@@ -169,7 +169,8 @@ def time_lpc1(torch, ch, stream, steps, warmup):
     cells = W["nx"] ** 3 * W["nk"] ** 3
     return {"value": cells * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "steps": steps, "dtype": "f32", "mass_drift": (m1 - m0) / m0,
-            "note": "LPC1 (Sec. 2.2): 2 Theta applications, 6 advection passes, 1 combine per step"}
+            "note": "LPC1 (Sec. 2.2): 2 Theta applications and 6 advection passes per step (the "
+                    "predictor and corrector base are formed inside the Theta kernel)"}
 
 
 def aggregate_ranks(ms_local: float, cells: int, steps: int, dist=None, device="cpu"):
@@ -221,6 +222,23 @@ def time_pflow_launches(torch, s, f, dt, stream, reps):
     torch.cuda.synchronize()
     del g
     return e0.elapsed_time(e1) / reps
+
+
+def host_copy_gbs(torch, host, dev, stream):
+    """Plain pinned host <-> device copy bandwidth of one f-sized buffer on this machine (GB/s,
+    CUDA events), reported beside the end-to-end number: its copies move these bytes."""
+    out = {}
+    for name, dst, src in (("h2d", dev, host), ("d2h", host, dev)):
+        with torch.cuda.stream(stream):
+            dst.copy_(src, non_blocking=True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = host.numel() * host.element_size() / (e0.elapsed_time(e1) / 1e3) / 1e9
+    return out
 
 
 def cpu_baseline(seconds_target: float = 20.0):
@@ -367,7 +385,8 @@ def run_chasm(args):
                 entry["e2e"] = {"value": world * cells * k_e2e / t_e2e, "unit": UNIT,
                                 "h2d_bytes_per_step": s.f_bytes() / k_e2e,
                                 "d2h_bytes_per_step": (s.f_bytes() + 8) / k_e2e,
-                                "steps": k_e2e}
+                                "steps": k_e2e, "wall_s": t_e2e,
+                                "host_copy_gbs": host_copy_gbs(torch, host, f, stream)}
                 del host, hout
             del f
             s.close()
