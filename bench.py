@@ -419,8 +419,9 @@ def run_chasm(args):
     peak = fp32_alu_peak_tflops()
     try:
         fma32, fma64 = ch.chasm.fma_peaks()
+        fma32x2 = ch.chasm.fma_peak_f32x2()
     except Exception:
-        fma32 = fma64 = None
+        fma32 = fma64 = fma32x2 = None
     tr = committed_traffic()
     line = {
         "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
@@ -443,6 +444,7 @@ def run_chasm(args):
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                      "measured_fma_peak_tflops": fma32,
                      "frac_of_measured_fma_peak": (achieved / fma32) if fma32 else None,
+                     "measured_packed_f32x2_fma_tflops": fma32x2,
                      "ms_per_launch": r32["pflow_ms"],
                      "flops_per_launch": flops_launch,
                      "traffic": (tr["dram_bytes_per_launch"] * cells / tr["cells"]) if tr else None},

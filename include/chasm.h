@@ -213,6 +213,11 @@ int chasm_expectations(chasm_handle* h, const void* f_dev, double* out_host);
  * measurement utility for roofline reports. */
 int chasm_fma_peaks(double* fp32_tflops, double* fp64_tflops);
 
+/* The same measurement with the packed single-precision FMA (two FP32 FMAs per instruction on
+ * register pairs, sm_100 and later), four flops per instruction, in TFLOP/s: whether the pairs
+ * raise the FP32 arithmetic ceiling or only halve the instructions issued.  Synchronous. */
+int chasm_fma_peak_f32x2(double* tflops);
+
 /* Mass and energy exactly as chasm_moments defines them, for callers that cannot allocate
  * device memory when they need them: code running while a stream is captured in the global
  * capture mode (cudaMalloc is not allowed then), services that reserve their whole memory budget

@@ -152,3 +152,27 @@ def test_diagnostics_match_oracle_and_are_reproducible(ch, name, nk, nx):
         e = np.array(s.expectations(f))
         assert np.allclose(e, O.expectations(fo, prob), rtol=0, atol=1e-12)
         assert np.array_equal(e, np.array(s.expectations(f)))
+
+
+@pytest.mark.parametrize("name", ["fp64", "fp32"])
+@pytest.mark.parametrize("nk", [16, 32])
+def test_lpc1_table_form_with_patches_matches_oracle(ch, name, nk):
+    """LPC1 in the table form at N_k = 16 and 32 (the Theta kernel forms the predictor and the
+    corrector base itself) with p > 1 PMBC patches in two x-dimensions: steps against the
+    oracle's LPC1 combination (Sec. 2.2) of its patch advection and Theta."""
+    patches = (3, 2, 1)
+    prob = O.Problem(nx=(7, 5, 4), nk=nk, x_lo=(-3.0, -2.5, -2.0), x_hi=(3.5, 2.0, 2.5), lk=4.0,
+                     nuclei=[((0.35, -0.2, 0.15), 1.0)], n_nb=4)
+    f0 = rough_input(prob, 31)
+    dt, nsteps = 0.015, (2 if nk == 16 else 1)   # the oracle's N_k = 32 Theta takes seconds
+    with solver(ch, prob, name, "table", patches=patches) as s:
+        f = to_dev(f0, name)
+        s.step(f, dt, nsteps)
+        s.sync()
+        got = f.double().cpu().numpy()
+    T = O.tkm_tensor(prob.nk, prob.lk)
+    ref = oracle_input(f0, name)
+    for _ in range(nsteps):
+        ref = O.lpc1_combine(ref, lambda u: O.advect_patches(u, prob, dt, patches),
+                             lambda u: O.theta(u, prob, T), dt)
+    assert O.rel_l2(got, ref) <= TOL[name], O.rel_l2(got, ref)
