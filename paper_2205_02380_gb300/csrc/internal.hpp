@@ -88,6 +88,13 @@ cudaError_t measure_fma_peak_f32x2(double* tflops);
 // the per-x symbol table (k_xsym.cu), [nxp][N][2N][2N] in the storage type; needs H.d_T
 size_t xs_table_bytes(int nk, int64_t nxp, size_t elt);
 cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s);
+// Split-half combine of the table-form slab phase (single precision, N_k = 32): the symbol table
+// carries the sign pattern (-1)^jj on the parity-1 runs, which shifts the parity-1 lane's inverse
+// transforms along k1 by N/2 so that each lane of a pair keeps a contiguous half of the column
+// without selects (k_xsym.cu writes the signs, fft_reg.cuh uses them).
+template <typename T, int N>
+__host__ __device__ constexpr bool xs_split() { return sizeof(T) == 4 && N == 32; }
+
 constexpr size_t kXsAutoMaxBytes = (size_t)64 << 30;   // CHASM_THETA_AUTO limit without a device
 // symbol precompute (k_symbol.cu): T (FP64, (2N-1)^3) and T-hat (parity-major, scaled)
 cudaError_t compute_symbol(int nk, double lk, double* T_dev, void* that_dev, bool fp64,

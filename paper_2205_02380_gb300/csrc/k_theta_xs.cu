@@ -21,6 +21,7 @@
 // Per x point (one CTA, persistent loop over x points):
 //   Phase A   N^2 lines along k3: twist, FFT_N -> G[j][k1][k2]
 //   Phase B   N slabs j: the 2-D padded convolution in (k1, k2) (slab_conv), spectrum times i sigma
+//             (single precision, N = 32: the column combines split in halves, xs_split)
 //   Phase CA  N^2 lines: inverse FFT_N along k3, conjugate twist, real part = Theta line;
 //             v = base + c_s Theta.  After the last stage v is written out; otherwise the same
 //             thread twists and transforms v in place of the next stage's Phase A (same lines,
@@ -61,7 +62,9 @@ struct XsCfg {
   static constexpr int SR = GSM ? N + 1 : N;   // spectrum row stride (padded in shared memory)
   static constexpr int SLAB = N * SR;
   static_assert(NT % GS == 0 && (GS <= 32 || NG <= 15), "slab groups must tile the CTA");
-  static constexpr size_t smem_cpx = (size_t)NG * N * VLayout<N>::VR + (GSM ? (size_t)N * SLAB : 0);
+  static constexpr bool SPLIT = xs_split<T, N>();
+  static constexpr int VSIZE = VRows<T, N, SPLIT>::SIZE;   // group slab buffer, elements
+  static constexpr size_t smem_cpx = (size_t)NG * VSIZE + (GSM ? (size_t)N * SLAB : 0);
   static constexpr size_t smem_bytes = smem_cpx * sizeof(cpx<T>);
 };
 
@@ -199,8 +202,8 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
   cpx<T>* smem = reinterpret_cast<cpx<T>*>(sm_raw);
   const int tid = threadIdx.x;
   const int grp = tid / GS, tg = tid % GS;
-  cpx<T>* V = smem + grp * (N * VLayout<N>::VR);
-  cpx<T>* G = GSM ? smem + NG * N * VLayout<N>::VR : p.G + (size_t)blockIdx.x * (N * SLAB);
+  cpx<T>* V = smem + grp * C::VSIZE;
+  cpx<T>* G = GSM ? smem + NG * C::VSIZE : p.G + (size_t)blockIdx.x * (N * SLAB);
   const uint64_t pol = l2_keep_policy();
 
   for (int64_t xp = blockIdx.x; xp < p.nxp; xp += gridDim.x) {
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
           const int64_t xn = s + NG < N || st + 1 < p.nst ? xp : xp + gridDim.x;
           if (xn < p.nxp) bulk_prefetch_l2(p.sig + (xn * N + sn) * (int64_t)(L * L), L * L * sizeof(T));
         }
-        slab_conv<T, N, GS, SR, !GSM, true>(G + (size_t)s * SLAB, V,
+        slab_conv<T, N, GS, SR, !GSM, true, C::SPLIT>(G + (size_t)s * SLAB, V,
                                             p.sig + (xp * N + s) * (int64_t)(L * L), tg, grp, pol);
       }
       __syncthreads();
