@@ -371,7 +371,7 @@ def run_chasm(args):
             if prec_name == "fp32":
                 # end-to-end through the C ABI with HOST buffers (pinned), copies included
                 host = torch.empty(f.shape, dtype=dtp, pin_memory=True)
-                host.copy_(f.cpu())
+                host.copy_(f)
                 hout = torch.empty_like(host, pin_memory=True)
                 k_e2e = max(1, min(steps, args.e2e_steps))
                 s.run_host(host.data_ptr(), hout.data_ptr(), dt, 1)   # warm: buffer + graph
