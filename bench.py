@@ -67,6 +67,15 @@ def fp32_alu_peak_tflops() -> float:
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def measured_hbm_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the 6.8 TB/s
+    fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 def theta_source_hash() -> str:
     """Hash of the sources of the P(dt) kernel (the traffic figure is void once they change)."""
     h = hashlib.sha256()
@@ -570,6 +579,74 @@ def run_serve_mode(args):
     print(json.dumps(out), flush=True)
 
 
+def run_kernels(args):
+    """Achieved bandwidth of the HBM-bound kernels outside the Strang step's pair (reductions,
+    diagnostics, the quadratic-potential P-flow and Theta), FP32-mixed, on the full 32^3 x 32^3
+    grid: algorithmic bytes per call / time per call.  Asynchronous calls are timed with CUDA
+    events on the solver's stream; calls that return host values (they synchronise) by the wall
+    clock around a synchronised loop, so their figure includes the call's return latency."""
+    import torch
+    import paper_2205_02380_gb300 as ch
+    W = WORKLOAD
+    n, nk = W["nx"], W["nk"]
+    fb = n ** 3 * nk ** 3 * 4
+    peak = measured_hbm_gbs()
+    stream = torch.cuda.Stream()
+    res = {}
+
+    def ev_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def wall_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / reps
+
+    def put(name, kernels, ms, nbytes, how):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        res[name] = {"kernels": kernels, "ms": ms, "algorithmic_bytes": nbytes, "gbs": gbs,
+                     "frac_of_measured_hbm": (gbs / peak) if peak else None, "timing": how}
+
+    shape = (n,) * 3 + (nk,) * 3
+    with torch.cuda.stream(stream):
+        s = make_solver(ch, ch.FP32_MIXED, stream)
+        f = torch.empty(shape, device="cuda", dtype=torch.float32)
+        s.init_hydrogen_1s(f, n_y=W["n_y"])
+        put("mass_energy", "k_moments", wall_ms(lambda: s.moments(f), 5), fb, "wall")
+        for j in range(3):
+            put(f"reduced_wigner_{j}", "k_diag_kpart + k_diag_wigner",
+                wall_ms(lambda: s.reduced_wigner(f, j), 3), fb, "wall")
+        put("expectations", "3 x k_diag_kpart + k_diag_expect", wall_ms(lambda: s.expectations(f), 3),
+            3 * fb, "wall")
+        s.close()
+        del f
+        torch.cuda.empty_cache()
+        h = ch.Solver(n, nk, -W["L"], W["L"], W["lk"], kappa=1.0, precision=ch.FP32_MIXED,
+                      stream=stream.cuda_stream)
+        f = torch.empty(shape, device="cuda", dtype=torch.float32)
+        h.init_gaussians(f, [{"w": math.pi ** -3, "x0": (1.0, -0.5, 0.3), "k0": (0.5, 0.2, -0.4),
+                              "ax": 0.5, "ak": 2.0}])
+        put("harmonic_pflow", "3 x k_kshift", ev_ms(lambda: h.pflow(f, 1e-3), 5), 6 * fb, "events")
+        out = torch.empty_like(f)
+        put("harmonic_theta", "3 x k_kderiv", ev_ms(lambda: h.theta(f, out), 5), 8 * fb, "events")
+        h.close()
+    print(json.dumps({"kernels": res, "workload": "32^3 x 32^3 FP32 (f = %.1f GB)" % (fb / 1e9),
+                      "peak_gbs": peak}))
+
+
 def run_profile(args):
     """FP32 form only: init, W warm-up steps and K steps, nothing else (for ncu)."""
     import torch
@@ -601,6 +678,8 @@ def main():
     ap.add_argument("--acc-steps", type=int, default=4)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-lpc1", action="store_true")
+    ap.add_argument("--kernels", action="store_true",
+                    help="bandwidth of the reduction, diagnostic and quadratic-potential kernels")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--rate", type=float, default=5.0)
     ap.add_argument("--slots", type=int, default=8)
@@ -615,6 +694,9 @@ def main():
         WORKLOAD["name"] = WORKLOAD["name"].replace("32^3x32^3", f"{args.nx}^3x32^3")
     if args.profile:
         run_profile(args)
+        return
+    if args.kernels:
+        run_kernels(args)
         return
     if args.serve:
         run_serve_mode(args)

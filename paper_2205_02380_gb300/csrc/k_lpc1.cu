@@ -5,7 +5,8 @@
 //                   spectral derivative on the periodic k-grid (i xi_m, xi_m = pi m / L_k, the
 //                   Nyquist mode dropped), applied as its circulant: (D u)_p = sum_j d_j u_{p-j},
 //                   d_j = -(2/N) sum_{m=1}^{N/2-1} xi_m sin(2 pi m j / N).  One thread per k-line,
-//                   the N taps in the kernel's parameter block (constant-bank operands).
+//                   the N taps in the kernel's parameter block (constant-bank operands); the
+//                   k3 pass (k_kderiv3) stages its contiguous lines in shared memory.
 //   k_lpc1_combine  predictor and corrector base from the advected fields g = f(A_dt) and
 //                   h = Theta[f](A_dt): v = g + dt h (the predictor f~), f = g + dt/2 h.
 #include "internal.hpp"
@@ -67,6 +68,48 @@ __global__ void __launch_bounds__(128) k_kderiv(const KDerivParams<T, N> p) {
   }
 }
 
+// The k3 pass (contiguous lines): a block stages LB consecutive lines of in and of the term it
+// adds to (out or base) in shared memory with coalesced loads (row stride N + 1), each thread
+// forms its line in registers, and the block stores the tile coalesced.
+template <typename T, int N>
+struct KDeriv3 {
+  static constexpr int LB = (sizeof(T) == 8 && N == 32) ? 64 : 128;   // lines per block
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(KDeriv3<T, N>::LB) k_kderiv3(const KDerivParams<T, N> p) {
+  constexpr int LB = KDeriv3<T, N>::LB;
+  __shared__ T tin[LB][N + 1];
+  __shared__ T tb[LB][N + 1];
+  const int tid = threadIdx.x;
+  const int64_t lines = p.nxp * N * N;
+  const int64_t l0 = (int64_t)blockIdx.x * LB;
+  const int nl = lines - l0 < LB ? (int)(lines - l0) : LB;
+  const T* b = p.accumulate ? p.out : p.base;   // the term added to (null: none)
+  for (int i = tid; i < nl * N; i += LB) {
+    tin[i / N][i % N] = p.in[l0 * N + i];
+    tb[i / N][i % N] = b ? b[l0 * N + i] : (T)0;
+  }
+  __syncthreads();
+  if (tid < nl) {
+    const int64_t xp = (l0 + tid) / (N * N);
+    const int id = (int)(xp % p.nx3);
+    const T scale = (T)(p.rate_scale * (p.x_lo + id * p.h - p.center)) * p.coef;
+    T v[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) v[l] = tin[tid][l];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T acc = (T)0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) acc = fma(p.d[(q - l + N) & (N - 1)], v[l], acc);
+      tb[tid][q] = fma(scale, acc, tb[tid][q]);
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < nl * N; i += LB) p.out[l0 * N + i] = tb[i / N][i % N];
+}
+
 template <typename T>
 __global__ void k_lpc1_combine(T* __restrict__ f, const T* __restrict__ h, T* __restrict__ v, int64_t n,
                                T dt) {
@@ -117,7 +160,10 @@ cudaError_t kderiv_tn(const Handle& H, const void* in, const void* base, void* o
     p.x_lo = H.g.x_lo[d];
     p.h = H.g.h[d];
     p.center = H.center[d];
-    k_kderiv<T, N><<<nb, 128, 0, s>>>(p);
+    if (d == 2)
+      k_kderiv3<T, N><<<nblk(H.g.nxp * N * N, KDeriv3<T, N>::LB), KDeriv3<T, N>::LB, 0, s>>>(p);
+    else
+      k_kderiv<T, N><<<nb, 128, 0, s>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

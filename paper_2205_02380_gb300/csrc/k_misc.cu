@@ -61,6 +61,86 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const T* __restrict__ f
   }
 }
 
+// Single precision: the FP64 pipe (1/64 of the FP32 rate on this part) cannot keep up with one
+// FP64 add per element at HBM speed, so each thread sums runs of 32 elements in compensated FP32
+// pairs (Knuth's error-free two-sum; the products v |k|^2 with their exact FMA residual) and
+// adds each run's (hi, lo) to FP64 accumulators: about 2^-44 relative per run, the same fixed
+// order on every call (bitwise reproducible), float4 loads.
+__device__ __forceinline__ void two_sum_f(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (v - bb);
+  hi = s;
+}
+
+template <>
+__global__ void __launch_bounds__(kMomThreads) k_moments<float>(const float* __restrict__ f, int64_t nxp,
+                                                                int nk, const double* __restrict__ vx,
+                                                                double* __restrict__ partials) {
+  __shared__ double red[2][kMomThreads / 32];
+  const int tid = threadIdx.x;
+  const int lg = __ffs(nk) - 1;              // nk is a power of two
+  const int kvol4 = (nk * nk * nk) >> 2;     // float4 per x point
+  const int half = nk >> 1;
+  constexpr int kRun = 8;                    // float4 loads per compensated run (32 elements)
+  double bm = 0.0, bk = 0.0, bv = 0.0;       // block accumulators (thread 0)
+  for (int64_t xp = blockIdx.x; xp < nxp; xp += gridDim.x) {
+    const float4* fx = reinterpret_cast<const float4*>(f + xp * (int64_t)(kvol4 << 2));
+    double s0 = 0.0, s2 = 0.0;
+    int e4 = tid;
+    while (e4 < kvol4) {
+      float h0 = 0.f, l0 = 0.f, h2 = 0.f, l2 = 0.f;
+#pragma unroll
+      for (int r = 0; r < kRun; ++r) {
+        if (e4 < kvol4) {
+          const float4 q = __ldcs(fx + e4);
+          const float v[4] = {q.x, q.y, q.z, q.w};
+          const int e = e4 << 2;
+          const int k1 = (e >> (2 * lg)) - half, k2 = ((e >> lg) & (nk - 1)) - half;
+          const int k3b = (e & (nk - 1)) - half;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int k3 = k3b + c;
+            const float w = (float)(k1 * k1 + k2 * k2 + k3 * k3);   // exact: at most 3 (nk/2)^2
+            two_sum_f(h0, l0, v[c]);
+            const float pr = v[c] * w;
+            l2 += fmaf(v[c], w, -pr);                                 // exact product residual
+            two_sum_f(h2, l2, pr);
+          }
+        }
+        e4 += kMomThreads;
+      }
+      s0 += (double)h0 + (double)l0;
+      s2 += (double)h2 + (double)l2;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = s0;
+      red[1][tid >> 5] = s2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < kMomThreads / 32; ++w) {
+        a += red[0][w];
+        b += red[1][w];
+      }
+      bm += a;
+      bk += b;
+      bv += vx[xp] * a;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    partials[(int64_t)3 * blockIdx.x + 0] = bm;
+    partials[(int64_t)3 * blockIdx.x + 1] = bk;
+    partials[(int64_t)3 * blockIdx.x + 2] = bv;
+  }
+}
+
 __global__ void k_moments_final(const double* __restrict__ partials, int nblocks, double cell,
                                 double kin_fac, double* __restrict__ out) {
   __shared__ double red[3][kMomThreads];
@@ -130,6 +210,43 @@ __global__ void k_kshift(T* __restrict__ f, int64_t nxp, int nx1, int nx2, int n
     for (int l = 0; l < N; ++l) acc += c[(j - l + N) & (N - 1)] * v[l];
     f[base + j * stride] = acc;
   }
+}
+
+// The k3 pass: the lines are contiguous, so a thread walking its own line would touch a new cache
+// line with every load of its warp.  A block stages its kKsLines consecutive lines in shared memory
+// with coalesced loads (row stride N + 1: conflict-free line reads), each thread applies the
+// circulant to its line in registers, and the block writes the tile back coalesced.
+constexpr int kKsLines = 128;
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kKsLines) k_kshift3(T* __restrict__ f, int64_t nxp, int nx1, int nx2,
+                                                      int nx3, const T* __restrict__ rows) {
+  __shared__ T tile[kKsLines][N + 1];
+  const int tid = threadIdx.x;
+  const int64_t lines = nxp * N * N;
+  const int64_t l0 = (int64_t)blockIdx.x * kKsLines;   // first line of the block
+  const int nl = lines - l0 < kKsLines ? (int)(lines - l0) : kKsLines;
+  T* g = f + l0 * N;
+  for (int i = tid; i < nl * N; i += kKsLines) tile[i / N][i % N] = g[i];
+  __syncthreads();
+  if (tid < nl) {
+    const int64_t xp = (l0 + tid) / (N * N);
+    const T* crow = rows + (int64_t)(nx1 + nx2 + (int)(xp % nx3)) * N;
+    T c[N], v[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) c[q] = __ldg(crow + q);
+#pragma unroll
+    for (int l = 0; l < N; ++l) v[l] = tile[tid][l];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      T acc = (T)0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) acc += c[(j - l + N) & (N - 1)] * v[l];
+      tile[tid][j] = acc;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < nl * N; i += kKsLines) g[i] = tile[i / N][i % N];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -277,8 +394,15 @@ cudaError_t launch_kshift(const Handle& H, void* f, int dim, const void* rows, c
   const int64_t lines = H.g.nxp * H.g.nk * H.g.nk;
   const unsigned nb = nblk(lines, 128);
   const int* nx = H.g.nx;
-#define CHASM_KS(TT, NN) \
-  k_kshift<TT, NN><<<nb, 128, 0, s>>>((TT*)f, H.g.nxp, nx[0], nx[1], nx[2], dim, (const TT*)rows)
+#define CHASM_KS(TT, NN)                                                                           \
+  do {                                                                                             \
+    if (dim == 2)                                                                                  \
+      k_kshift3<TT, NN><<<nblk(lines, kKsLines), kKsLines, 0, s>>>((TT*)f, H.g.nxp, nx[0], nx[1],  \
+                                                                   nx[2], (const TT*)rows);        \
+    else                                                                                           \
+      k_kshift<TT, NN><<<nb, 128, 0, s>>>((TT*)f, H.g.nxp, nx[0], nx[1], nx[2], dim,               \
+                                          (const TT*)rows);                                        \
+  } while (0)
   switch (H.g.nk) {
     case 8:
       if (H.fp64) CHASM_KS(double, 8); else CHASM_KS(float, 8);
