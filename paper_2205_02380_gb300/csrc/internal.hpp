@@ -95,7 +95,18 @@ cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s);
 template <typename T, int N>
 __host__ __device__ constexpr bool xs_split() { return sizeof(T) == 4 && N == 32; }
 
-constexpr size_t kXsAutoMaxBytes = (size_t)64 << 30;   // CHASM_THETA_AUTO limit without a device
+constexpr size_t kXsAutoMaxBytes = (size_t)64 << 30;
+
+#ifdef __CUDACC__
+// hi + lo += v with Knuth's error-free two-sum (the rounding error of hi + v goes to lo): the
+// compensated single-precision sums of the reductions
+__device__ __forceinline__ void two_sum_f(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (v - bb);
+  hi = s;
+}
+#endif   // CHASM_THETA_AUTO limit without a device
 // symbol precompute (k_symbol.cu): T (FP64, (2N-1)^3) and T-hat (parity-major, scaled)
 cudaError_t compute_symbol(int nk, double lk, double* T_dev, void* that_dev, bool fp64,
                            double* that_absmax_host, cudaStream_t s);

@@ -34,6 +34,38 @@ __global__ void k_diag_kpart(const T* __restrict__ f, int64_t nxp, int d, double
   S[t] = s;
 }
 
+// Single precision: each row of N elements is summed in compensated FP32 (two-sum) and added to
+// the FP64 total (the FP64 pipe runs at 1/64 of the FP32 rate here); rows along k3 read 16 bytes
+// at a time.
+template <int N>
+__global__ void k_diag_kpart_f(const float* __restrict__ f, int64_t nxp, int d, double* __restrict__ S) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nxp * N) return;
+  const int64_t xp = t / N;
+  const int q = (int)(t % N);
+  const float* fx = f + xp * (N * N * N);
+  double s = 0.0;
+  for (int a = 0; a < N; ++a) {
+    float hi = 0.f, lo = 0.f;
+    if (d == 2) {
+#pragma unroll 8
+      for (int b = 0; b < N; ++b) two_sum_f(hi, lo, fx[(a * N + b) * N + q]);
+    } else {
+      const float4* row = reinterpret_cast<const float4*>(fx + (d == 0 ? (q * N + a) * N : (a * N + q) * N));
+#pragma unroll
+      for (int b4 = 0; b4 < N / 4; ++b4) {
+        const float4 v = row[b4];
+        two_sum_f(hi, lo, v.x);
+        two_sum_f(hi, lo, v.y);
+        two_sum_f(hi, lo, v.z);
+        two_sum_f(hi, lo, v.w);
+      }
+    }
+    s += (double)hi + (double)lo;
+  }
+  S[t] = s;
+}
+
 // W_j[i][q] = vol * sum over the other two x indices (ascending) of S_j[x][q]
 __global__ void k_diag_wigner(const double* __restrict__ S, int j, int nx0, int nx1, int nx2, int N,
                               double vol, double* __restrict__ W) {
@@ -105,8 +137,12 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <typename T, int N>
 cudaError_t kpart_tn(const Handle& H, const void* f, int d, double* S, cudaStream_t s) {
-  k_diag_kpart<T, N><<<nblk(H.g.nxp * N, kDiagThreads), kDiagThreads, 0, s>>>(
-      static_cast<const T*>(f), H.g.nxp, d, S + (size_t)d * H.g.nxp * N);
+  if constexpr (sizeof(T) == 4)
+    k_diag_kpart_f<N><<<nblk(H.g.nxp * N, kDiagThreads), kDiagThreads, 0, s>>>(
+        static_cast<const float*>(f), H.g.nxp, d, S + (size_t)d * H.g.nxp * N);
+  else
+    k_diag_kpart<T, N><<<nblk(H.g.nxp * N, kDiagThreads), kDiagThreads, 0, s>>>(
+        static_cast<const T*>(f), H.g.nxp, d, S + (size_t)d * H.g.nxp * N);
   return cudaGetLastError();
 }
 

@@ -66,12 +66,6 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const T* __restrict__ f
 // pairs (Knuth's error-free two-sum; the products v |k|^2 with their exact FMA residual) and
 // adds each run's (hi, lo) to FP64 accumulators: about 2^-44 relative per run, the same fixed
 // order on every call (bitwise reproducible), float4 loads.
-__device__ __forceinline__ void two_sum_f(float& hi, float& lo, float v) {
-  const float s = hi + v;
-  const float bb = s - hi;
-  lo += (hi - (s - bb)) + (v - bb);
-  hi = s;
-}
 
 template <>
 __global__ void __launch_bounds__(kMomThreads) k_moments<float>(const float* __restrict__ f, int64_t nxp,
