@@ -547,13 +547,36 @@ def run_serving(ch, n_req, rate, seed, nx_choices, nk_choices, steps, precisions
         wall = time.perf_counter() - t0
     finally:
         srv.close()
-    lat = sorted(r.latency_ms for r in res)
-    work = sum(r.cells * r.nsteps for r in res)
-    pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
-    return {"requests": len(res), "failed": sum(1 for r in res if r.status != 0),
-            "rate_per_s": rate, "p50_ms": pct(0.50), "p99_ms": pct(0.99),
-            "mean_queue_ms": statistics.mean(r.queue_ms for r in res),
-            "cell_updates_per_s": work / wall, "wall_s": wall}
+    out = serving_stats([(sp["precision"], r.latency_ms, r.queue_ms, r.cells * r.nsteps, r.status)
+                         for sp, r in zip(specs, res)], wall)
+    out["rate_per_s"] = rate
+    return out
+
+
+def latency_percentile(sorted_ms, q):
+    """Nearest-rank percentile of an ascending list."""
+    return sorted_ms[min(len(sorted_ms) - 1, max(0, int(math.ceil(q * len(sorted_ms))) - 1))]
+
+
+def serving_stats(rows, wall):
+    """Latency percentiles and throughput of a served stream from (precision, latency_ms,
+    queue_ms, cell-updates, status) per request; with more than one precision in the stream also
+    per precision (latencies of the requests of that precision in the same mixed run)."""
+    def block(rs):
+        lat = sorted(r[1] for r in rs)
+        return {"requests": len(rs), "failed": sum(1 for r in rs if r[4] != 0),
+                "p50_ms": latency_percentile(lat, 0.50), "p99_ms": latency_percentile(lat, 0.99),
+                "mean_queue_ms": statistics.mean(r[2] for r in rs),
+                "cell_updates": sum(r[3] for r in rs)}
+    out = block(rows)
+    out["cell_updates_per_s"] = out.pop("cell_updates") / wall
+    out["wall_s"] = wall
+    precs = sorted({r[0] for r in rows})
+    if len(precs) > 1:
+        names = {0: "fp32_mixed", 1: "fp64"}
+        out["by_precision"] = {names.get(p, str(p)): block([r for r in rows if r[0] == p])
+                               for p in precs}
+    return out
 
 
 def run_serve_mode(args):

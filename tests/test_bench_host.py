@@ -65,3 +65,19 @@ def test_serving_stream_is_seeded_and_keeps_nuclei_off_the_nodes():
             for c in pos:
                 t = (c + s["L"]) / h
                 assert abs(t - round(t)) * h >= h / 4 - 1e-12
+
+
+def test_serving_stats_percentiles_and_per_precision_split():
+    import bench
+    rows = [(0, float(10 * i), 1.0, 100, 0) for i in range(1, 11)] + \
+           [(1, float(1000 + i), 2.0, 50, 0) for i in range(1, 5)]
+    st = bench.serving_stats(rows, wall=2.0)
+    assert st["requests"] == 14 and st["failed"] == 0
+    assert st["p50_ms"] == 70.0                 # nearest rank 7 of 14
+    assert st["p99_ms"] == 1004.0
+    assert st["cell_updates_per_s"] == pytest.approx((10 * 100 + 4 * 50) / 2.0)
+    fp32, fp64 = st["by_precision"]["fp32_mixed"], st["by_precision"]["fp64"]
+    assert (fp32["requests"], fp32["p50_ms"], fp32["p99_ms"]) == (10, 50.0, 100.0)
+    assert (fp64["requests"], fp64["p50_ms"], fp64["p99_ms"]) == (4, 1002.0, 1004.0)
+    one = bench.serving_stats(rows[:10], wall=1.0)
+    assert "by_precision" not in one and one["p99_ms"] == 100.0
