@@ -81,3 +81,38 @@ def test_serving_stats_percentiles_and_per_precision_split():
     assert (fp64["requests"], fp64["p50_ms"], fp64["p99_ms"]) == (4, 1002.0, 1004.0)
     one = bench.serving_stats(rows[:10], wall=1.0)
     assert "by_precision" not in one and one["p99_ms"] == 100.0
+
+
+def test_run_serving_end_to_end_with_a_fake_server():
+    """bench.run_serving's submission loop and statistics against a stand-in for the server
+    binding (the real one needs a GPU): results come back in ticket order, one per request."""
+    import types
+    import bench
+
+    class FakeServer:
+        def __init__(self, budget, max_slots, steps_per_launch, queue_capacity):
+            self.reqs = []
+
+        def submit(self, req):
+            self.reqs.append(req)
+            return len(self.reqs) - 1
+
+        def wait(self, ticket, timeout):
+            r = self.reqs[ticket]
+            return types.SimpleNamespace(latency_ms=10.0 + ticket, queue_ms=1.0,
+                                         cells=r["cells"], nsteps=r["nsteps"], status=0)
+
+        def close(self):
+            pass
+
+    def make_request(nx, nk, lo, hi, lk, dt, nsteps, nuclei, packets, precision):
+        return {"cells": nx ** 3 * nk ** 3, "nsteps": nsteps, "precision": precision}
+
+    ch = types.SimpleNamespace(Server=FakeServer, make_request=make_request)
+    out = bench.run_serving(ch, n_req=6, rate=1e6, seed=7, nx_choices=(16,), nk_choices=(16,),
+                            steps=(10, 12), precisions=(0, 1), budget=1 << 30, max_slots=2, spl=5)
+    assert out["requests"] == 6 and out["failed"] == 0 and out["rate_per_s"] == 1e6
+    assert out["p99_ms"] == 15.0 and out["cell_updates_per_s"] > 0
+    specs = bench.serving_specs(7, 6, (16,), (16,), (10, 12), (0, 1))
+    if len({s["precision"] for s in specs}) > 1:
+        assert sum(b["requests"] for b in out["by_precision"].values()) == 6
