@@ -296,7 +296,6 @@ struct VLayout {
   static constexpr int VH = N >= 16 ? N + 8 : N;
   static constexpr int VR = VH + N + 1;
   static constexpr int D = N >= 16 ? 8 : N / 2;   // lane h keeps the elements m with (m / D) % 2 == h
-  __device__ static constexpr int col(int c) { return (c / N) * VH + (c % N); }
 };
 
 // Rows of V for the split-half combine: rows r >= N/2 start PAD elements (64 bytes) later, so that
@@ -509,19 +508,6 @@ __device__ __forceinline__ void load_line(const T* __restrict__ src, T (&v)[N]) 
       v[2 * q] = (T)t.x;
       v[2 * q + 1] = (T)t.y;
     }
-  }
-}
-
-template <typename T, int N>
-__device__ __forceinline__ void store_line(T* __restrict__ dst, const T (&v)[N]) {
-  if constexpr (sizeof(T) == 4 && N % 4 == 0) {
-    float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-    for (int q = 0; q < N / 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-  } else {
-    double2* d2 = reinterpret_cast<double2*>(dst);
-#pragma unroll
-    for (int q = 0; q < N / 2; ++q) d2[q] = make_double2(v[2 * q], v[2 * q + 1]);
   }
 }
 
