@@ -72,20 +72,25 @@ class Problem:
     n_nb: int = 20
 
     def xs(self, d: int) -> np.ndarray:
+        """x-nodes of dimension d, ends included (Sec. 3: N + 1 points)."""
         return x_nodes(self.nx[d], self.x_lo[d], self.x_hi[d])
 
     def hs(self, d: int) -> float:
+        """x-spacing of dimension d."""
         return (self.x_hi[d] - self.x_lo[d]) / (self.nx[d] - 1)
 
     def ks(self) -> np.ndarray:
+        """k-nodes (j - N_k/2) dk, the same in every dimension (Sec. 4.1, k_zeta = zeta dk)."""
         return k_nodes(self.nk, self.lk)
 
     @property
     def dk(self) -> float:
+        """k-spacing 2 L_k / N_k."""
         return 2.0 * self.lk / self.nk
 
     @property
     def shape(self) -> tuple:
+        """Shape of f: (nx1, nx2, nx3, N_k, N_k, N_k), k3 fastest."""
         return tuple(self.nx) + (self.nk,) * 3
 
     def potential(self) -> np.ndarray:
@@ -541,6 +546,7 @@ def strang_step_plane(g: np.ndarray, prob: Problem, d: int, dt: float) -> np.nda
 
 
 def pflow(f: np.ndarray, prob: Problem, dt: float, T=None) -> np.ndarray:
+    """P(dt): the Coulomb Taylor-4 flow when the problem has nuclei, else the exact k-shift."""
     if prob.nuclei:
         return pflow_coulomb(f, prob, dt, T)
     return pflow_harmonic(f, prob, dt)
@@ -554,6 +560,7 @@ def strang_step(f: np.ndarray, prob: Problem, dt: float, T=None) -> np.ndarray:
 
 
 def run(f: np.ndarray, prob: Problem, dt: float, nsteps: int) -> np.ndarray:
+    """nsteps Strang steps (T computed once)."""
     T = tkm_tensor(prob.nk, prob.lk) if prob.nuclei else None
     for _ in range(nsteps):
         f = strang_step(f, prob, dt, T)
@@ -630,6 +637,7 @@ def lpc1_step_plane(g: np.ndarray, prob: Problem, d: int, dt: float) -> np.ndarr
 
 
 def run_lpc1(f: np.ndarray, prob: Problem, dt: float, nsteps: int) -> np.ndarray:
+    """nsteps LPC1 steps (Sec. 2.2; T computed once)."""
     T = tkm_tensor(prob.nk, prob.lk) if prob.nuclei else None
     for _ in range(nsteps):
         f = lpc1_step(f, prob, dt, T)

@@ -21,12 +21,15 @@ FP32_MIXED, FP64 = 0, 1
 
 
 class ChasmError(RuntimeError):
+    """A negative status of the C ABI with chasm_last_error's message; .code is the status."""
+
     def __init__(self, code: int, msg: str):
         super().__init__(f"chasm error {code}: {msg}")
         self.code = code
 
 
 class Grid(C.Structure):
+    """chasm_grid (include/chasm.h)."""
     _fields_ = [("nx", C.c_int32 * 3), ("nk", C.c_int32 * 3)]
 
 
@@ -44,6 +47,7 @@ class Potential(C.Structure):
 
 
 class Options(C.Structure):
+    """chasm_options (include/chasm.h); fill with chasm_options_default first."""
     _fields_ = [("precision", C.c_int32), ("n_nb", C.c_int32), ("patches", C.c_int32 * 3),
                 ("use_graphs", C.c_int32), ("cuda_stream", C.c_void_p), ("theta_form", C.c_int32),
                 ("integrator", C.c_int32)]
@@ -147,17 +151,20 @@ def _ptr(t) -> int:
 
 
 def make_grid(nx, nk) -> Grid:
+    """chasm_grid: nx points per x-dimension (an int or three ints), N_k points per k-dimension."""
     nx = list(nx) if hasattr(nx, "__len__") else [nx] * 3
     return Grid((C.c_int32 * 3)(*nx), (C.c_int32 * 3)(nk, nk, nk))
 
 
 def make_box(x_lo, x_hi, lk) -> Box:
+    """chasm_box: x in [x_lo, x_hi] per dimension (ends included), k in [-lk, lk)."""
     x_lo = list(x_lo) if hasattr(x_lo, "__len__") else [x_lo] * 3
     x_hi = list(x_hi) if hasattr(x_hi, "__len__") else [x_hi] * 3
     return Box((C.c_double * 3)(*x_lo), (C.c_double * 3)(*x_hi), (C.c_double * 3)(lk, lk, lk))
 
 
 def make_gaussian(w, x0, k0, ax, ak) -> Gaussian:
+    """chasm_gaussian: w exp(-ax |x - x0|^2 - ak |k - k0|^2)."""
     return Gaussian(w, (C.c_double * 3)(*x0), (C.c_double * 3)(*k0), ax, ak)
 
 
@@ -208,6 +215,7 @@ class Solver:
         self.shape = tuple(nxx) + (nk,) * 3
 
     def close(self):
+        """chasm_destroy: frees the handle's workspace (idempotent)."""
         if getattr(self, "h", None):
             lib().chasm_destroy(self.h)
             self.h = None
@@ -244,40 +252,52 @@ class Solver:
 
     # --- calls ---
     def num_cells(self) -> int:
+        """N_x1 N_x2 N_x3 N_k^3."""
         return lib().chasm_num_cells(self.h)
 
     def f_bytes(self) -> int:
+        """Bytes of f in this handle's precision."""
         return lib().chasm_f_bytes(self.h)
 
     def set_stream(self, stream_ptr):
+        """chasm_set_stream: issue later work on the cudaStream_t stream_ptr."""
         _check(lib().chasm_set_stream(self.h, stream_ptr), self.h)
 
     def sync(self):
+        """chasm_sync: wait for the handle's stream."""
         self._call(lib().chasm_sync)
 
     def step(self, f, dt, nsteps=1):
+        """chasm_step: nsteps time steps of size dt on f in place (Strang or LPC1, as created);
+        raises ChasmError(EUNSTABLE) when dt exceeds the stability bound."""
         self._call(lib().chasm_step, _ptr(f), dt, nsteps)
 
     def advect(self, f, tau):
+        """chasm_advect: the spatial advection A(tau) alone, in place."""
         self._call(lib().chasm_advect, _ptr(f), tau)
 
     def pflow(self, f, dt):
+        """chasm_pflow: the potential flow P(dt) alone, in place."""
         self._call(lib().chasm_pflow, _ptr(f), dt)
 
     def theta(self, u, out):
+        """chasm_theta: out = Theta^T[u] (the Coulomb operator, or kappa (x - c)/hbar . grad_k u)."""
         self._call(lib().chasm_theta, _ptr(u), _ptr(out))
 
     def moments(self, f):
+        """chasm_moments: (mass, energy) of f, FP64, bitwise reproducible."""
         m, e = C.c_double(), C.c_double()
         self._call(lib().chasm_moments, _ptr(f), C.byref(m), C.byref(e))
         return m.value, e.value
 
     def mass(self, f) -> float:
+        """chasm_mass: h1 h2 h3 dk^3 sum f."""
         m = C.c_double()
         self._call(lib().chasm_mass, _ptr(f), C.byref(m))
         return m.value
 
     def energy(self, f) -> float:
+        """chasm_energy: h1 h2 h3 dk^3 sum (hbar^2 |k|^2 / 2m + V(x)) f."""
         e = C.c_double()
         self._call(lib().chasm_energy, _ptr(f), C.byref(e))
         return e.value
@@ -291,6 +311,7 @@ class Solver:
         return out
 
     def marginal_x12(self, f):
+        """P(x1, x2) as a (nx[0], nx[1]) float64 numpy array."""
         import numpy as np
         out = np.zeros((self.shape[0], self.shape[1]))
         self._call(lib().chasm_marginal_x12, _ptr(f), out.ctypes.data_as(C.POINTER(C.c_double)))
@@ -303,15 +324,19 @@ class Solver:
         return tuple(out)
 
     def init_gaussians(self, f, packets):
+        """chasm_init_gaussians: f = sum of the packets, each a dict w, x0, k0, ax, ak."""
         arr = (Gaussian * len(packets))(*[make_gaussian(p["w"], p["x0"], p["k0"], p["ax"], p["ak"])
                                           for p in packets])
         self._call(lib().chasm_init_gaussians, _ptr(f), arr, len(packets))
 
     def init_hydrogen_1s(self, f, n_y=128, center=(0.0, 0.0, 0.0)):
+        """chasm_init_hydrogen_1s: the 1s Wigner function centred at center, from n_y^3 samples
+        of the position-space orbital per k-direction."""
         c = (C.c_double * 3)(*center)
         self._call(lib().chasm_init_hydrogen_1s, _ptr(f), n_y, c)
 
     def tkm_tensor(self, out_ptr):
+        """chasm_tkm_tensor: the FP64 truncated-kernel tensor T into host memory at out_ptr."""
         self._call(lib().chasm_tkm_tensor, C.cast(out_ptr, C.POINTER(C.c_double)))
 
     def run_host(self, f0_ptr, fout_ptr, dt, nsteps) -> float:
@@ -322,6 +347,7 @@ class Solver:
 
 def workspace_bytes(nx, nk, nuclei=(), kappa=0.0, precision=FP32_MIXED, n_nb=20,
                     theta_form=THETA_AUTO, integrator=STRANG) -> int:
+    """chasm_workspace_bytes: device bytes a handle with these settings allocates besides f."""
     L = lib()
     g = make_grid(nx, nk)
     nuc = (Nucleus * max(1, len(nuclei)))(*[Nucleus((C.c_double * 3)(*p), z) for p, z in nuclei])
@@ -381,6 +407,8 @@ class Server:
 
 def make_request(nx, nk, x_lo, x_hi, lk, dt, nsteps, nuclei=(), kappa=0.0, packets=(),
                  precision=FP32_MIXED, hbar=1.0, m=1.0, n_nb=20, f0_ptr=None, fout_ptr=None) -> Request:
+    """chasm_request for the server: the solve's grid, box, potential, dt and steps, its initial
+    data (Gaussian packets, or a host buffer f0_ptr) and an optional host output buffer."""
     r = Request()
     r.grid = make_grid(nx, nk)
     r.box = make_box(x_lo, x_hi, lk)

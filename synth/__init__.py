@@ -28,6 +28,7 @@ class SplitMix64:
         self.state = seed & MASK64
 
     def next_u64(self) -> int:
+        """The next 64-bit output."""
         self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
         z = self.state
         z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
@@ -44,6 +45,7 @@ class SplitMix64:
 
 
 def axes(nx, nk, x_lo, x_hi, lk):
+    """The x-node arrays per dimension (ends included) and the k-nodes (j - N_k/2) dk."""
     xs = [x_lo[d] + np.arange(nx[d]) * ((x_hi[d] - x_lo[d]) / (nx[d] - 1)) for d in range(3)]
     ks = (np.arange(nk) - nk / 2) * (2.0 * lk / nk)
     return xs, ks
