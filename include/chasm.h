@@ -113,7 +113,8 @@ typedef struct {
 typedef struct {
   int32_t precision;    /* CHASM_FP32_MIXED (default) or CHASM_FP64                         */
   int32_t n_nb;         /* PMBC stencil length n_nb of Eq. 3.2 (default 20, >= 1)           */
-  int32_t patches[3];   /* patches per x-dimension p (Sec. 3.1); only p = 1 is implemented  */
+  int32_t patches[3];   /* PMBC patches per x-dimension p (Sec. 3.1.3; default 1): p divides
+                           nx - 1 and leaves at least 2 intervals per patch, else EINVAL     */
   int32_t use_graphs;   /* 1 (default): chasm_step replays a captured CUDA graph per step   */
   void* cuda_stream;    /* cudaStream_t to run on; NULL: the handle creates its own stream  */
   int32_t theta_form;   /* CHASM_THETA_AUTO (default), CHASM_THETA_TABLE, CHASM_THETA_MODULATED */
