@@ -695,10 +695,20 @@ def expectations(f: np.ndarray, prob: Problem) -> np.ndarray:
     return out
 
 
-def errors(f_ref: np.ndarray, f_num: np.ndarray, prob: Problem):
-    """(eps_inf, eps_2) of Sec. 5 with the integral as the grid sum times the cell volume."""
+def errors(f_ref: np.ndarray, f_num: np.ndarray, prob):
+    """(eps_inf, eps_2) of Sec. 5: the largest |f_ref - f_num| over the grid, and the square root
+    of the integral of (f_ref - f_num)^2 with the integral as the grid sum times the cell volume.
+    prob is a Problem (cell h1 h2 h3 dk^3) or the cell volume itself (e.g. dk^3 for a function of k
+    alone, as in Example 4.1)."""
+    vol = cell_volume(prob) if isinstance(prob, Problem) else float(prob)
     d = f_ref - f_num
-    return float(np.max(np.abs(d))), float(np.sqrt(np.sum(d * d) * cell_volume(prob)))
+    return float(np.max(np.abs(d))), float(np.sqrt(np.sum(d * d) * vol))
+
+
+def mass_error(f_num: np.ndarray, f_ref0: np.ndarray, prob: Problem) -> float:
+    """eps_mass of Sec. 5: |integral of (f_num(t) - f_ref(0))|, the integral as the grid sum times
+    the cell volume."""
+    return float(abs(np.sum(f_num - f_ref0)) * cell_volume(prob))
 
 
 def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
