@@ -220,20 +220,22 @@ int chasm_fma_peaks(double* fp32_tflops, double* fp64_tflops);
 int chasm_fma_peak_f32x2(double* tflops);
 
 /* Mass and energy exactly as chasm_moments defines them, for callers that cannot allocate
- * device memory when they need them: code running while a stream is captured in the global
- * capture mode (cudaMalloc is not allowed then), services that reserve their whole memory budget
- * for solves up front, plug-ins that only receive a device pointer.  The paper has no
- * counterpart; this is a library convenience.  It needs no handle and allocates nothing: its
- * scratch is a fixed device array of 3 * 262144 + 2 doubles (6 MiB) that the library reserves on
- * every GPU that loads it until the process exits.  Hence at most 262144 x points
- * (nx1 nx2 nx3, e.g. 64^3); larger grids are rejected with EINVAL and a message.  f_dev has the
- * layout and element type (precision) of chasm_step; grid, box and potential are validated as
- * in chasm_create; mass/energy are host pointers (either may be NULL, not both).  Work runs on
- * cuda_stream (NULL = legacy default stream) and the call waits for it.  The first call on each
- * device looks up the array's device address with that device current; make that first call
- * before any stream capture begins.  All calls share the one array and it keeps the last call's
- * contents (every entry a call reads is written by that call first), so calls whose work
- * overlaps on the GPU race with each other: serialise them. */
+ * device memory when they need them: services that hand their whole device-memory budget to
+ * solves up front (an allocation for a check could then fail or push the device past the budget)
+ * and plug-ins that only receive a device pointer from a host framework that owns all device
+ * memory.  The paper has no counterpart; this is a library convenience.  It needs no handle and
+ * allocates nothing: its scratch is a fixed device array of 3 * 262144 + 2 doubles (6 MiB) that
+ * the library reserves on every GPU that loads it until the process exits.  Hence at most 262144
+ * x points (nx1 nx2 nx3, e.g. 64^3); larger grids are rejected with EINVAL and a message.  f_dev
+ * has the layout and element type (precision) of chasm_step; grid, box, potential, hbar and m pass
+ * the checks of chasm_create (else EINVAL); mass/energy are host pointers (either may be NULL, not
+ * both).  Work runs on cuda_stream (NULL = the legacy default stream) and the call waits for it.
+ * The first call on each device, with that device current, looks up the array's device address
+ * and loads the entry point's kernels; the address is kept for the device's primary context (the
+ * one the CUDA runtime uses), so the entry point must not be called again after cudaDeviceReset.
+ * All calls share the one array and it keeps the last call's contents (every entry a call reads
+ * is written by that call first), so calls whose work overlaps on the GPU race with each other:
+ * serialise them. */
 int chasm_moments_noalloc(const void* f_dev, const chasm_grid* grid, const chasm_box* box,
                           const chasm_potential* pot, double hbar, double m, int32_t precision,
                           void* cuda_stream, double* mass, double* energy);

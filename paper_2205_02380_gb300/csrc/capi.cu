@@ -634,6 +634,11 @@ int issue_step(Handle* H, void* f, double dt) {
 
 void set_thread_error(const std::string& e) { g_thread_err = e; }
 
+std::string validate_problem(const chasm_grid* grid, const chasm_box* box, const chasm_potential* pot,
+                             double hbar, double m) {
+  return validate(grid, box, pot, hbar, m, nullptr);
+}
+
 }  // namespace chasm
 
 using namespace chasm;

@@ -185,4 +185,9 @@ struct Handle {
 // Returns a message for the last error on this thread when no handle exists.
 void set_thread_error(const std::string& e);
 
+// The checks chasm_create applies to grid, box (may be NULL), potential, hbar and m; an empty
+// string when they pass, else the message.
+std::string validate_problem(const chasm_grid* grid, const chasm_box* box, const chasm_potential* pot,
+                             double hbar, double m);
+
 }  // namespace chasm

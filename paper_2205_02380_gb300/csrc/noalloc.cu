@@ -1,13 +1,13 @@
 // chasm_moments_noalloc: mass and energy of a caller's f without allocating any memory.
 //
-// Some callers cannot allocate device memory at the moment they need these diagnostics: code
-// running while another stream is being captured in the global capture mode (where cudaMalloc
-// is not permitted), services that reserve the whole device-memory budget up front for their
-// solves (the serving loop of this library is one), and plug-ins that only receive a device
-// pointer from a host framework that owns all memory.  chasm_moments needs a handle, and a handle
-// allocates its tables and work buffers; this variant needs neither.  Its scratch (one partial
-// sum triple per x point and the two results) is a fixed file-scope device array, so the
-// library reserves that memory on every GPU that loads it, for as long as the process lives.
+// Some callers cannot allocate device memory at the moment they need these diagnostics:
+// services that hand their whole device-memory budget to solves up front (the serving loop of
+// this library admits requests against such a budget, so a check that allocated could push the
+// device past it or fail with out-of-memory), and plug-ins that only receive a device pointer from
+// a host framework that owns all device memory and its allocator.  chasm_moments needs a handle,
+// and a handle allocates its tables and work buffers; this variant needs neither.  Its scratch
+// (one partial-sum triple per x point and the two results) is a fixed file-scope device array, so
+// the library reserves that memory on every GPU that loads it, for as long as the process lives.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -112,7 +112,11 @@ __global__ void __launch_bounds__(kThreads) k_moments_total(const double* __rest
   }
 }
 
-// Device address of the scratch array, looked up once per device (with that device current).
+// Per-device set-up, done once with that device current: the device address of the scratch
+// array (in host code the array's name is only a host-side stand-in) and the loading of the three
+// kernels (with lazy module loading a kernel's first launch would otherwise load its code then,
+// which needs device memory).  The cached address belongs to the device's primary context, the
+// one the CUDA runtime uses.
 std::mutex g_addr_mu;
 double* g_addr[kMaxDevices] = {};
 
@@ -120,7 +124,11 @@ cudaError_t scratch_address(int dev, double** out) {
   std::lock_guard<std::mutex> lk(g_addr_mu);
   if (!g_addr[dev]) {
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_moments_per_x<float>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_moments_per_x<double>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_moments_total);
     if (e != cudaSuccess) return e;
     g_addr[dev] = static_cast<double*>(p);
   }
@@ -144,22 +152,12 @@ extern "C" int chasm_moments_noalloc(const void* f_dev, const chasm_grid* grid, 
     set_thread_error("moments_noalloc: precision must be CHASM_FP32_MIXED or CHASM_FP64");
     return CHASM_EINVAL;
   }
-  for (int d = 0; d < 3; ++d)
-    if (grid->nx[d] < 4 || !(box->x_hi[d] > box->x_lo[d]) || !(box->k_half[d] > 0)) {
-      set_thread_error("moments_noalloc: nx >= 4, x_hi > x_lo and k_half > 0 are required");
-      return CHASM_EINVAL;
-    }
+  const std::string bad = validate_problem(grid, box, pot, hbar, m);
+  if (!bad.empty()) {
+    set_thread_error("moments_noalloc: " + bad);
+    return CHASM_EINVAL;
+  }
   const int nk = grid->nk[0];
-  if ((nk != 8 && nk != 16 && nk != 32) || grid->nk[1] != nk || grid->nk[2] != nk ||
-      box->k_half[1] != box->k_half[0] || box->k_half[2] != box->k_half[0]) {
-    set_thread_error("moments_noalloc: nk in {8, 16, 32} and a cubic k-box are required");
-    return CHASM_EINVAL;
-  }
-  if (pot->n_nuc < 0 || pot->n_nuc > kMaxNuclei || (pot->n_nuc > 0 && !pot->nuc) || !(hbar > 0) ||
-      !(m > 0)) {
-    set_thread_error("moments_noalloc: 0 <= n_nuc <= 8, hbar > 0 and m > 0 are required");
-    return CHASM_EINVAL;
-  }
   const int64_t nxp = (int64_t)grid->nx[0] * grid->nx[1] * grid->nx[2];
   if (nxp > kNoallocMaxXPoints) {
     set_thread_error("moments_noalloc: at most " + std::to_string(kNoallocMaxXPoints) +
@@ -190,16 +188,22 @@ extern "C" int chasm_moments_noalloc(const void* f_dev, const chasm_grid* grid, 
   }
   a.kappa = pot->harm_kappa;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  if (precision == CHASM_FP64)
-    k_moments_per_x<double><<<(unsigned)nxp, kThreads, 0, s>>>((const double*)f_dev, a, scratch);
-  else
-    k_moments_per_x<float><<<(unsigned)nxp, kThreads, 0, s>>>((const float*)f_dev, a, scratch);
+  // cudaLaunchKernel returns the status of this launch itself, so an earlier error of the
+  // caller's own code is neither reported here nor cleared
+  const void* fptr = f_dev;
+  void* args1[] = {(void*)&fptr, (void*)&a, (void*)&scratch};
+  e = cudaLaunchKernel(precision == CHASM_FP64 ? (const void*)k_moments_per_x<double>
+                                               : (const void*)k_moments_per_x<float>,
+                       dim3((unsigned)nxp), dim3(kThreads), args1, 0, s);
   const double dk = 2.0 * box->k_half[0] / nk;
-  const double cell = a.h[0] * a.h[1] * a.h[2] * dk * dk * dk;
+  double cell = a.h[0] * a.h[1] * a.h[2] * dk * dk * dk;
+  double kin = hbar * hbar / (2.0 * m) * dk * dk;
+  int64_t n = nxp;
   double* res = scratch + 3 * kNoallocMaxXPoints;
-  k_moments_total<<<1, kThreads, 0, s>>>(scratch, nxp, cell, hbar * hbar / (2.0 * m) * dk * dk, res);
+  void* args2[] = {(void*)&scratch, (void*)&n, (void*)&cell, (void*)&kin, (void*)&res};
+  if (e == cudaSuccess)
+    e = cudaLaunchKernel((const void*)k_moments_total, dim3(1), dim3(kThreads), args2, 0, s);
   double out[2];
-  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, sizeof(out), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
