@@ -1,9 +1,12 @@
 """Benchmark: 6-D cell-updates per second of one Strang step of the CHASM scheme on GB300.
 
-Workload (default): hydrogen 1s stationarity, V = -1/|x|, grid 32^3 x 32^3 on [-12,12]^3 x
-[-4,4)^3 (1.07e9 cells), dt = 0.025, initial f = the 1s Wigner function (discrete Fourier sum,
-N_y = 128) written on the GPU.  The headline `value` is the FP32-mixed form; the FP64 form is
-measured on the same GPU and reported under "fp64".
+Headline workload (`value`): the two-centre Coulomb problem V = -1/|x - a| - 1/|x + a|,
+a = (0.7, 0, 0), on 64^3 x 32^3 cells over [-16,16]^3 x [-4,4)^3 (8.6e9 cells, 34 GB per FP32
+copy of f), initial f the seeded mixture of two unit-mass packets (SplitMix64 seed 2205),
+dt = 0.02, FP32-mixed form: the largest of the paper-shaped workloads that fits one GPU.  The FP64
+form is timed on the largest workload whose FP64 table form fits one GPU, the electron-proton case
+48^3 x 32^3 on [-12,12]^3 ("fp64", next to the FP32-mixed form on the same workload), and the
+hydrogen 1s stationarity test 32^3 x 32^3 runs its 40 steps in both forms ("stationarity").
 
 Prints ONE JSON line (rank 0).  Under torchrun with N > 1 every rank runs its own replica of the
 workload on its own GPU (no data-path collective) and `value` is the sum over ranks of cells
@@ -30,11 +33,45 @@ sys.path.insert(0, ROOT)
 METRIC = "6-D cell-updates/s per Strang step, FP32-mixed vs FP64 at stated L2 error"
 UNIT = "cell-updates/s"
 
-WORKLOAD = {
-    "name": "hydrogen-1s 32^3x32^3 [-12,12]^3 x [-4,4)^3, V=-1/|x|, dt=0.025",
-    "nx": 32, "nk": 32, "L": 12.0, "lk": 4.0, "dt": 0.025,
-    "nuclei": [((0.0, 0.0, 0.0), 1.0)], "n_y": 128,
+# The paper-shaped workloads (Sec. 5.2-5.4), all with hbar = m = 1 and L_k = 4.
+#   init: ("gauss", seed or packet list) or ("1s", N_y)
+WORKLOADS = {
+    "two-centre": {
+        "name": "two-centre 64^3x32^3 [-16,16]^3 x [-4,4)^3, V=-1/|x-a|-1/|x+a|, a=(0.7,0,0), "
+                "seeded two-packet mixture (seed 2205), dt=0.02",
+        "nx": 64, "nk": 32, "L": 16.0, "lk": 4.0, "dt": 0.02,
+        "nuclei": [((0.7, 0.0, 0.0), 1.0), ((-0.7, 0.0, 0.0), 1.0)],
+        "init": ("mixture", 2205)},
+    "electron-proton": {
+        "name": "electron-proton 48^3x32^3 [-12,12]^3 x [-4,4)^3, V=-1/|x|, packet at (-4,0,0) "
+                "with k0=(1,0,0), dt=0.02",
+        "nx": 48, "nk": 32, "L": 12.0, "lk": 4.0, "dt": 0.02,
+        "nuclei": [((0.0, 0.0, 0.0), 1.0)],
+        "init": ("packet", ((-4.0, 0.0, 0.0), (1.0, 0.0, 0.0)))},
+    "hydrogen-1s": {
+        "name": "hydrogen-1s 32^3x32^3 [-12,12]^3 x [-4,4)^3, V=-1/|x|, dt=0.025",
+        "nx": 32, "nk": 32, "L": 12.0, "lk": 4.0, "dt": 0.025,
+        "nuclei": [((0.0, 0.0, 0.0), 1.0)],
+        "init": ("1s", 128)},
 }
+HEADLINE = "two-centre"
+FP64_WORKLOAD = "electron-proton"
+STATIONARITY = "hydrogen-1s"
+
+
+def cells_of(W) -> int:
+    return W["nx"] ** 3 * W["nk"] ** 3
+
+
+def packets_of(W):
+    """Initial packets of a Gaussian workload (synth's unit-mass packets)."""
+    import synth
+    kind, arg = W["init"]
+    if kind == "mixture":
+        return synth.two_packet_mixture(arg)
+    if kind == "packet":
+        return [synth.packet(*arg)]
+    raise ValueError(kind)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -57,14 +94,14 @@ def theta_flops_per_cell(nk: int) -> float:
     return total / n ** 3
 
 
-def fp32_alu_peak_tflops() -> float:
-    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x the maximum SM clock."""
+def fp32_alu_peak_tflops(num_sms: int) -> float:
+    """SMs (read from the device) x 128 FP32 lanes x 2 flops (FMA) x the maximum SM clock."""
     mhz = 2070.0
     try:
         mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
     except Exception:
         pass
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+    return num_sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
 def measured_hbm_gbs():
@@ -153,33 +190,28 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------------
-def make_solver(ch, precision, stream, integrator=None):
-    W = WORKLOAD
+def make_solver(ch, W, precision, stream, integrator=None):
     return ch.Solver(W["nx"], W["nk"], -W["L"], W["L"], W["lk"], nuclei=W["nuclei"],
                      precision=precision, stream=stream.cuda_stream, theta_form=ch.THETA_TABLE,
                      integrator=ch.STRANG if integrator is None else integrator)
 
 
-def time_lpc1(torch, ch, stream, steps, warmup):
-    """The paper's LPC1 integrator on the same workload (FP32-mixed, table form): W untimed and
-    `steps` timed steps, CUDA events on the solver's stream."""
-    W = WORKLOAD
-    with torch.cuda.stream(stream):
-        s = make_solver(ch, ch.FP32_MIXED, stream, ch.LPC1)
-        f = torch.empty((W["nx"],) * 3 + (W["nk"],) * 3, device="cuda", dtype=torch.float32)
-        s.init_hydrogen_1s(f, n_y=W["n_y"])
-        m0 = s.mass(f)
-        ms = time_steps(torch, s, f, W["dt"], steps, warmup, stream, None)
-        m1 = s.mass(f)
-        s.close()
-        del f
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
-    cells = W["nx"] ** 3 * W["nk"] ** 3
-    return {"value": cells * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
-            "steps": steps, "dtype": "f32", "mass_drift": (m1 - m0) / m0,
-            "note": "LPC1 (Sec. 2.2): 2 Theta applications and 6 advection passes per step (the "
-                    "predictor and corrector base are formed inside the Theta kernel)"}
+def init_f(s, W, f):
+    """Writes the workload's initial f on the GPU (chasm_init_gaussians / chasm_init_hydrogen_1s)."""
+    kind, arg = W["init"]
+    if kind == "1s":
+        s.init_hydrogen_1s(f, n_y=arg)
+    else:
+        s.init_gaussians(f, packets_of(W))
+
+
+def new_f(torch, W, dtp):
+    return torch.empty((W["nx"],) * 3 + (W["nk"],) * 3, device="cuda", dtype=dtp)
+
+
+def release(torch):
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
 
 def aggregate_ranks(ms_local: float, cells: int, steps: int, dist=None, device="cpu"):
@@ -197,8 +229,8 @@ def aggregate_ranks(ms_local: float, cells: int, steps: int, dist=None, device="
 
 
 def time_steps(torch, s, f, dt, steps, warmup, stream, dist):
-    """W untimed steps, then exactly `steps` Strang steps between CUDA events on the solver's
-    stream, bracketed by barrier + synchronize.  Returns milliseconds."""
+    """W untimed steps, then exactly `steps` steps between CUDA events on the solver's stream,
+    bracketed by barrier + synchronize.  Returns milliseconds."""
     s.step(f, dt, warmup)
     torch.cuda.synchronize()
     if dist:
@@ -250,90 +282,311 @@ def host_copy_gbs(torch, host, dev, stream):
     return out
 
 
-def cpu_baseline(seconds_target: float = 20.0):
-    """Runs the FP64 oracle on a bounded sample of the workload in a fresh single-threaded
-    process and returns its throughput (see oracle_sample)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
-                        "--sample-seconds", str(seconds_target)],
-                       capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": "failed: " + r.stderr[-300:]}
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def deviation_metrics(torch, a, b, vol):
+    """eps_inf = max |a - b| and eps_2 = sqrt(sum (a - b)^2 vol) (the error metrics of Sec. 5,
+    the integral as the grid sum times the cell volume), reduced in FP64 on a's device."""
+    d = a.double() - b.double()
+    return float(d.abs().max()), float(torch.sqrt((d * d).sum() * vol))
 
 
-def oracle_sample(seconds_target: float) -> dict:
-    """Times the oracle's three substeps on pieces of the full-size workload:
-    A(dt/2) on the full 32^3 x-cube at n_k sampled k points (the spline transform and the
-    64-tap sum are independent per k), and P(dt) (four Theta^T applications) at n_x sampled x
-    points (independent per x point).  Cell-update time = 2 t_A + t_P per cell."""
+# ------------------------------------------------------------------------------------------------
+# host-core baseline: the FP64 oracle on bounded pieces of the headline workload
+def host_info() -> dict:
+    """nproc and the CPU model of this machine."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            import platform
+            model = platform.processor() or platform.machine()
+        except Exception:
+            model = "unknown"
+    return {"nproc": os.cpu_count() or 1, "cpu_model": model}
+
+
+_T_CACHE = {}
+
+
+def _oracle_task(task):
+    """One independent piece of the oracle's step (runs in a worker process): ("A", k indices)
+    advects the full x-cube at those k points by dt/2; ("P", x index) applies P(dt) on the full
+    k-cube of one x point of the workload's initial data.  Returns (cells, seconds)."""
     import numpy as np
 
     import synth
     from oracle import chasm_oracle as O
-    W = WORKLOAD
+    kind, wname, idx = task
+    W = WORKLOADS[wname]
     nx, nk, L, lk, dt = W["nx"], W["nk"], W["L"], W["lk"], W["dt"]
     prob = O.Problem(nx=(nx,) * 3, nk=nk, x_lo=(-L,) * 3, x_hi=(L,) * 3, lk=lk,
                      nuclei=W["nuclei"])
-    ks = prob.ks()
-    # A: n_kA k points on the full x cube (surrogate smooth data; the cost is data independent)
-    xs = prob.xs(0)
-    g = np.exp(-0.5 * xs ** 2)
-    n_kA = 2
-    kidx = [(3, 17, 29), (20, 8, 14)][:n_kA]
-    cube = (g[:, None, None] * g[None, :, None] * g[None, None, :])[..., None, None, None]
-    t0 = time.perf_counter()
-    for (a, b, c) in kidx:
-        O.advect(cube, prob, 0.5 * dt, kaxes=(ks[a:a + 1], ks[b:b + 1], ks[c:c + 1]))
-    tA = (time.perf_counter() - t0) / (n_kA * nx ** 3)
-    # P: x points with the 1s data
-    T = O.tkm_tensor(nk, lk)
-    xpts = []
-    tP_total, n_xP = 0.0, 0
-    rng = np.random.default_rng(2205)
-    while n_xP < 2 or tP_total < seconds_target * 0.5:
-        i = rng.integers(0, nx, 3)
-        x = np.array([xs[i[0]], xs[i[1]], xs[i[2]]])
-        f1 = synth.wigner_1s((2, 2, 2), nk, tuple(x), tuple(x + 1.0), lk, n_y=W["n_y"])[:1, :1, :1]
+    if kind == "A":
+        # the spline transform and the 64-tap sum cost the same for any data: smooth surrogate
+        ks = prob.ks()
+        g = np.exp(-0.05 * prob.xs(0) ** 2)
+        cube = (g[:, None, None] * g[None, :, None] * g[None, None, :])[..., None, None, None]
+        a, b, c = idx
         t0 = time.perf_counter()
-        O.pflow_coulomb(f1.reshape(1, nk, nk, nk), prob, dt, T, xpts=x[None])
-        tP_total += time.perf_counter() - t0
-        n_xP += 1
-        xpts.append(x)
-        if n_xP >= 16:
-            break
-    tP = tP_total / (n_xP * nk ** 3)
-    t_cell = 2 * tA + tP
-    return {"value": 1.0 / t_cell, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, 1 thread: A(dt/2) on the full 32^3 x-cube at {n_kA} "
-                      f"k points ({tA * 1e6:.2f} us/cell) and P(dt) on {n_xP} x points of the 1s "
-                      f"data ({tP * 1e6:.2f} us/cell); cell-update time = 2 t_A + t_P"}
+        O.advect(cube, prob, 0.5 * dt, kaxes=(ks[a:a + 1], ks[b:b + 1], ks[c:c + 1]))
+        return nx ** 3, time.perf_counter() - t0
+    xs = prob.xs(0)
+    x = np.array([xs[idx[0]], xs[idx[1]], xs[idx[2]]])
+    # the initial data at the one x point (a 2-point grid starting there, first node kept)
+    if W["init"][0] == "1s":
+        f1 = synth.wigner_1s((2, 2, 2), nk, tuple(x), tuple(x + 1.0), lk, n_y=W["init"][1])
+    else:
+        f1 = synth.gaussian_packets((2, 2, 2), nk, tuple(x), tuple(x + 1.0), lk, packets_of(W))
+    f1 = f1[:1, :1, :1]
+    key = (nk, lk)
+    if key not in _T_CACHE:   # T is computed once per handle on the GPU side as well
+        _T_CACHE[key] = O.tkm_tensor(nk, lk)
+    T = _T_CACHE[key]
+    t0 = time.perf_counter()
+    O.pflow_coulomb(f1.reshape(1, nk, nk, nk), prob, dt, T, xpts=x[None])
+    return nk ** 3, time.perf_counter() - t0
+
+
+def oracle_pool(workers: int):
+    """A pool of `workers` spawned processes (no CUDA state is inherited) for oracle_sample."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    return cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+
+def oracle_sample(wname: str, workers: int, n_a: int, n_p: int, seed: int = 2205, ex=None) -> dict:
+    """Times the oracle on n_a k points of A(dt/2) (full x-cube each) and n_p x points of P(dt)
+    (full k-cube each), spread over `workers` processes (spawned, one thread each); the pieces are
+    independent, so the wall time of each batch gives that substep's cell rate on `workers` cores.
+    Cell-update time = 2 t_A + t_P.  ex: an oracle_pool to reuse (else one is made)."""
+    import numpy as np
+    W = WORKLOADS[wname]
+    nx, nk = W["nx"], W["nk"]
+    rng = np.random.default_rng(seed)
+    ka = [tuple(int(v) for v in rng.integers(0, nk, 3)) for _ in range(n_a)]
+    # x points where f is not negligible: near the nuclei and the packet centres
+    lo, h = -W["L"], 2 * W["L"] / (nx - 1)
+    centres = [p for p, _ in W["nuclei"]]
+    if W["init"][0] != "1s":
+        centres += [pk["x0"] for pk in packets_of(W)]
+    xp = []
+    for i in range(n_p):
+        c = centres[i % len(centres)]
+        xp.append(tuple(int(min(nx - 1, max(0, round((c[d] - lo) / h) + rng.integers(-2, 3))))
+                        for d in range(3)))
+    tasks_a = [("A", wname, k) for k in ka]
+    tasks_p = [("P", wname, x) for x in xp]
+    if workers == 1:
+        t0 = time.perf_counter()
+        ra = [_oracle_task(t) for t in tasks_a]
+        wa = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        rp = [_oracle_task(t) for t in tasks_p]
+        wp = time.perf_counter() - t0
+    else:
+        own = ex is None
+        if own:
+            ex = oracle_pool(workers)
+        try:
+            list(ex.map(_oracle_task, [("P", wname, xp[0])] * workers))   # imports, T, warm
+            t0 = time.perf_counter()
+            ra = list(ex.map(_oracle_task, tasks_a))
+            wa = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            rp = list(ex.map(_oracle_task, tasks_p))
+            wp = time.perf_counter() - t0
+        finally:
+            if own:
+                ex.shutdown()
+    tA = wa / sum(c for c, _ in ra)
+    tP = wp / sum(c for c, _ in rp)
+    return {"value": 1.0 / (2 * tA + tP), "t_a_us": tA * 1e6, "t_p_us": tP * 1e6,
+            "cpu_s": sum(t for _, t in ra) + sum(t for _, t in rp)}
+
+
+def cpu_baseline_run(wname: str, repeats: int = 3) -> dict:
+    """The oracle on all host cores and on one core, median of `repeats` bounded samples each."""
+    info = host_info()
+    n = info["nproc"]
+    W = WORKLOADS[wname]
+    out = {"unit": UNIT, "kind": "oracle", "cores": n, "cpu_model": info["cpu_model"],
+           "nproc": n}
+    with oracle_pool(n) as ex:
+        runs_all = [oracle_sample(wname, n, n_a=2 * n, n_p=8 * n, seed=2205 + r, ex=ex)
+                    for r in range(repeats)]
+    runs_one = [oracle_sample(wname, 1, n_a=2, n_p=8, seed=2205 + r) for r in range(repeats)]
+    med = lambda rs: statistics.median(r["value"] for r in rs)   # noqa: E731
+    out["value"] = med(runs_all)
+    out["value_all_cores"] = out["value"]
+    out["value_1_core"] = med(runs_one)
+    out["runs_all_cores"] = [r["value"] for r in runs_all]
+    out["runs_1_core"] = [r["value"] for r in runs_one]
+    out["sample"] = (
+        f"FP64 numpy oracle on {W['name']}: per run A(dt/2) on the full {W['nx']}^3 x-cube at "
+        f"2 k points per worker and P(dt) on the full {W['nk']}^3 k-cube at 8 x points per worker "
+        f"(near the nuclei and packet centres), {n} spawned single-threaded workers (all cores) or "
+        f"1; cell-update time 2 t_A + t_P; median of {repeats} runs each "
+        f"(all cores: t_A {runs_all[0]['t_a_us']:.3f} us, t_P {runs_all[0]['t_p_us']:.3f} us per cell)")
+    return out
+
+
+def cpu_baseline(wname: str) -> dict:
+    """Runs cpu_baseline_run in a fresh process with no GPU visible (threads pinned to one per
+    worker) and returns its result."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                        "--workload", wname], capture_output=True, text=True, env=env, timeout=1200)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                "sample": "failed: " + r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 # ------------------------------------------------------------------------------------------------
 def run_reference(args):
+    """The oracle as it stands on all host cores: each step one bounded sample of the headline
+    workload; value = median over the timed steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    info = host_info()
+    n = info["nproc"]
+    W = WORKLOADS[HEADLINE]
     per_step = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        r = oracle_sample(max(2.0, 60.0 / max(1, args.steps + args.warmup)))
-        if i >= args.warmup:
-            per_step.append(r["value"])
+    with oracle_pool(n) as ex:
+        for i in range(args.warmup + args.steps):
+            r = oracle_sample(HEADLINE, n, n_a=n, n_p=4 * n, seed=2205 + i, ex=ex)
+            if i >= args.warmup:
+                per_step.append(r["value"])
     value = statistics.median(per_step)
+    sample = (f"FP64 numpy oracle on {W['name']}, {n} spawned single-threaded workers: per step "
+              f"A(dt/2) on the full x-cube at {n} k points and P(dt) at {4 * n} x points; "
+              f"cell-update time 2 t_A + t_P")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "cells": WORKLOAD["nx"] ** 3 * WORKLOAD["nk"] ** 3,
+            "config": {"workload": W["name"], "cells": cells_of(W),
                        "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": r["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle",
+                             "cpu_model": info["cpu_model"], "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measure_form(torch, ch, W, prec, steps, warmup, stream, dist, sampler=None, e2e_steps=0,
+                 pflow_reps=1):
+    """Times `steps` steps of one form on one workload (plus P(dt) launches and, with e2e_steps,
+    the end-to-end host-buffer call).  Returns a dict."""
+    cells = cells_of(W)
+    dtp = torch.float32 if prec == ch.FP32_MIXED else torch.float64
+    with torch.cuda.stream(stream):
+        s = make_solver(ch, W, prec, stream)
+        f = new_f(torch, W, dtp)
+        init_f(s, W, f)
+        m0, en0 = s.moments(f)
+        if sampler:
+            sampler.start()
+        ms = time_steps(torch, s, f, W["dt"], steps, warmup, stream, dist)
+        clocks = sampler.stop() if sampler else None
+        m1, en1 = s.moments(f)
+        ms_t, value = aggregate_ranks(ms, cells, steps, dist, "cuda")
+        entry = {"value": value, "ms_per_step": ms_t / steps, "steps": steps, "warmup": warmup,
+                 "mass_drift": (m1 - m0) / m0, "energy0": en0, "energy": en1}
+        if clocks is not None:
+            entry["clocks"] = clocks
+        entry["pflow_ms"] = time_pflow_launches(torch, s, f, W["dt"], stream, pflow_reps)
+        if e2e_steps:
+            world = dist.get_world_size() if dist else 1
+            # end-to-end through the C ABI with HOST buffers (pinned), copies included
+            host = torch.empty(f.shape, dtype=dtp, pin_memory=True)
+            host.copy_(f)
+            hout = torch.empty_like(host, pin_memory=True)
+            s.run_host(host.data_ptr(), hout.data_ptr(), W["dt"], 1)   # warm: buffer + graph
+            runs = []
+            for _ in range(3):   # median of three calls (host-side timing noise)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.run_host(host.data_ptr(), hout.data_ptr(), W["dt"], e2e_steps)
+                runs.append(time.perf_counter() - t0)
+            t_e2e = statistics.median(runs)
+            entry["e2e"] = {"value": world * cells * e2e_steps / t_e2e, "unit": UNIT,
+                            "h2d_bytes_per_step": s.f_bytes() / e2e_steps,
+                            "d2h_bytes_per_step": (s.f_bytes() + 8) / e2e_steps,
+                            "steps": e2e_steps, "wall_s": t_e2e,
+                            "host_copy_gbs": host_copy_gbs(torch, host, f, stream)}
+            del host, hout
+        del f
+        s.close()
+    release(torch)
+    return entry
+
+
+def time_lpc1(torch, ch, W, stream, steps, warmup):
+    """The paper's LPC1 integrator on a workload (FP32-mixed, table form): W untimed and `steps`
+    timed steps, CUDA events on the solver's stream."""
+    with torch.cuda.stream(stream):
+        s = make_solver(ch, W, ch.FP32_MIXED, stream, ch.LPC1)
+        f = new_f(torch, W, torch.float32)
+        init_f(s, W, f)
+        m0 = s.mass(f)
+        ms = time_steps(torch, s, f, W["dt"], steps, warmup, stream, None)
+        m1 = s.mass(f)
+        s.close()
+        del f
+    release(torch)
+    return {"value": cells_of(W) * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "dtype": "f32", "workload": W["name"], "mass_drift": (m1 - m0) / m0,
+            "note": "LPC1 (Sec. 2.2): 2 Theta applications and 6 advection passes per step (the "
+                    "predictor and corrector base are formed inside the Theta kernel)"}
+
+
+def stationarity_run(torch, ch, stream, steps):
+    """Hydrogen 1s stationarity (Sec. 5.2): both forms from the same initial data for `steps`
+    steps.  Reports the relative L2 distance of the FP32-mixed result from the FP64 result (the
+    FP64 form is itself pinned to the FP64 oracle at 1e-12), and per form the drift of f from the
+    stationary initial state (eps_inf, eps_2 of Sec. 5 and relative L2), of the mass and of the
+    energy."""
+    W = WORKLOADS[STATIONARITY]
+    h = 2 * W["L"] / (W["nx"] - 1)
+    vol = h ** 3 * (2 * W["lk"] / W["nk"]) ** 3
+    out, finals = {}, {}
+    with torch.cuda.stream(stream):
+        for name, prec, dtp in (("fp64", ch.FP64, torch.float64), ("fp32", ch.FP32_MIXED, torch.float32)):
+            s = make_solver(ch, W, prec, stream)
+            f = new_f(torch, W, dtp)
+            init_f(s, W, f)
+            f0 = f.clone()
+            m0, e0 = s.moments(f)
+            s.step(f, W["dt"], steps)
+            m1, e1 = s.moments(f)
+            einf, e2 = deviation_metrics(torch, f, f0, vol)
+            rel = float(torch.linalg.vector_norm((f - f0).double()) / torch.linalg.vector_norm(f0.double()))
+            out[name] = {"eps_inf_vs_initial": einf, "eps_2_vs_initial": e2,
+                         "rel_l2_vs_initial": rel, "mass_drift": (m1 - m0) / m0,
+                         "energy0": e0, "energy_drift": (e1 - e0) / abs(e0)}
+            del f0
+            finals[name] = f
+            s.close()
+        a, b = finals["fp32"].double(), finals["fp64"]
+        rel = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        del a, b, finals
+    release(torch)
+    out.update({"workload": W["name"], "steps": steps, "t_final": steps * W["dt"],
+                "rel_l2_fp32_vs_fp64": rel, "tolerance": 1e-5,
+                "mass_rel_diff_fp32_vs_fp64": None,
+                "note": "the FP64 form is pinned to the FP64 oracle at <= 1e-12; eps_inf and eps_2 "
+                        "against the initial state, which is stationary for the exact flow"})
+    out["mass_rel_diff_fp32_vs_fp64"] = out["fp32"]["mass_drift"] - out["fp64"]["mass_drift"]
+    return out
 
 
 def run_chasm(args):
@@ -350,114 +603,78 @@ def run_chasm(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     ch.chasm.lib()
-    W = WORKLOAD
-    cells = W["nx"] ** 3 * W["nk"] ** 3
-    dt = W["dt"]
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    W = WORKLOADS[HEADLINE]
+    W64 = WORKLOADS[FP64_WORKLOAD]
+    cells = cells_of(W)
     stream = torch.cuda.Stream()
-    result = {}
 
     sampler = ClockSampler(local)
-    for prec_name, prec, steps in (("fp32", ch.FP32_MIXED, args.steps),
-                                   ("fp64", ch.FP64, max(1, min(args.steps, args.fp64_steps)))):
-        with torch.cuda.stream(stream):
-            s = make_solver(ch, prec, stream)
-            dtp = torch.float32 if prec == ch.FP32_MIXED else torch.float64
-            f = torch.empty((W["nx"],) * 3 + (W["nk"],) * 3, device="cuda", dtype=dtp)
-            s.init_hydrogen_1s(f, n_y=W["n_y"])
-            m0, e0 = s.moments(f)
-            if prec_name == "fp32":
-                sampler.start()
-            ms = time_steps(torch, s, f, dt, steps, args.warmup if prec_name == "fp32" else 1,
-                            stream, dist)
-            if prec_name == "fp32":
-                clocks = sampler.stop()
-            m1, e1 = s.moments(f)
-            ms_t, value = aggregate_ranks(ms, cells, steps, dist, "cuda")
-            entry = {"ms_per_step": ms_t / steps, "steps": steps, "value": value,
-                     "mass0": m0, "mass": m1, "energy0": e0, "energy": e1}
-            entry["pflow_ms"] = time_pflow_launches(torch, s, f, dt, stream,
-                                                    5 if prec_name == "fp32" else 1)
-            if prec_name == "fp32":
-                # end-to-end through the C ABI with HOST buffers (pinned), copies included
-                host = torch.empty(f.shape, dtype=dtp, pin_memory=True)
-                host.copy_(f)
-                hout = torch.empty_like(host, pin_memory=True)
-                k_e2e = max(1, min(steps, args.e2e_steps))
-                s.run_host(host.data_ptr(), hout.data_ptr(), dt, 1)   # warm: buffer + graph
-                runs = []
-                for _ in range(3):   # median of three calls (host-side timing noise)
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    s.run_host(host.data_ptr(), hout.data_ptr(), dt, k_e2e)
-                    runs.append(time.perf_counter() - t0)
-                t_e2e = statistics.median(runs)
-                entry["e2e"] = {"value": world * cells * k_e2e / t_e2e, "unit": UNIT,
-                                "h2d_bytes_per_step": s.f_bytes() / k_e2e,
-                                "d2h_bytes_per_step": (s.f_bytes() + 8) / k_e2e,
-                                "steps": k_e2e, "wall_s": t_e2e,
-                                "host_copy_gbs": host_copy_gbs(torch, host, f, stream)}
-                del host, hout
-            del f
-            s.close()
-            torch.cuda.synchronize()
-            torch.cuda.empty_cache()
-        result[prec_name] = entry
-
-    accuracy = accuracy_check(torch, ch, stream, args.acc_steps) if rank == 0 else None
-    # the host-core baseline runs after the GPU measurements: its large host allocations, made
-    # before the pinned e2e buffers, slowed the host <-> device copies of the e2e call (the child
-    # process shares no CUDA state)
-    base = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
-    lpc1 = time_lpc1(torch, ch, stream, max(1, args.steps), 1) if rank == 0 and not args.no_lpc1 else None
-    serving = None
-    if rank == 0 and not args.no_serving:
-        serving = run_serving(ch, n_req=16, rate=20.0, seed=2205, nx_choices=(16, 24),
-                              nk_choices=(16,), steps=(10, 30), precisions=(ch.FP32_MIXED,),
-                              budget=150 << 30, max_slots=8, spl=5)
-        serving["sample"] = ("16 requests, Poisson 20/s, nx in {16,24}, nk 16, 10-30 steps, "
-                             "FP32-mixed (the full 64-request stream: bench.py --serve)")
+    r32 = measure_form(torch, ch, W, ch.FP32_MIXED, args.steps, args.warmup, stream, dist,
+                       sampler=sampler, e2e_steps=max(1, args.e2e_steps), pflow_reps=3)
+    clocks = r32.pop("clocks")
+    r64 = measure_form(torch, ch, W64, ch.FP64, max(1, args.fp64_steps), 1, stream, dist)
+    r64_32 = measure_form(torch, ch, W64, ch.FP32_MIXED, max(1, min(args.steps, 5)), 2, stream,
+                          dist, pflow_reps=3)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    r32, r64 = result["fp32"], result["fp64"]
+    stat = stationarity_run(torch, ch, stream, args.stat_steps) if args.stat_steps > 0 else None
+    lpc1 = time_lpc1(torch, ch, W, stream, max(1, min(args.steps, 10)), 1) if not args.no_lpc1 else None
+    serving = None
+    if not args.no_serving:
+        serving = serving_both(ch, n_req=args.bench_serve_requests, rate=args.bench_serve_rate,
+                               steps=(10, 15))
+    # the host-core baseline runs after the GPU measurements (its host allocations slowed the
+    # pinned copies of the e2e call when made before them; the child process shares no CUDA state)
+    base = cpu_baseline(HEADLINE) if (world == 1 and not args.no_cpu_baseline) else None
+
     nk = W["nk"]
     flops_launch = 4 * theta_flops_per_cell(nk) * cells
     achieved = flops_launch / (r32["pflow_ms"] / 1e3) / 1e12
-    achieved64 = flops_launch / (r64["pflow_ms"] / 1e3) / 1e12
-    peak = fp32_alu_peak_tflops()
+    flops64 = 4 * theta_flops_per_cell(W64["nk"]) * cells_of(W64)
+    achieved64 = flops64 / (r64["pflow_ms"] / 1e3) / 1e12
+    peak = fp32_alu_peak_tflops(num_sms)
     try:
         fma32, fma64 = ch.chasm.fma_peaks()
         fma32x2 = ch.chasm.fma_peak_f32x2()
     except Exception:
         fma32 = fma64 = fma32x2 = None
     tr = committed_traffic()
+    e2e = r32.pop("e2e")
     line = {
         "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r32["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (hydrogen 1s Wigner function computed on the GPU)",
+        "data": "synthetic (seeded two-packet mixture written on the GPU)",
         "config": {"workload": W["name"], "cells": cells, "global_batch": world,
                    "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (f = %.1f GB)" % (cells * 4 / 1e9)},
-        "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
-                 "dtype": "f64", "pflow_ms": r64["pflow_ms"], "pflow_tflops": achieved64,
-                 "pflow_frac_of_measured_fp64_fma": (achieved64 / fma64) if fma64 else None},
-        "accuracy": accuracy,
+        "headline_detail": r32,
+        "fp64": {"workload": W64["name"], "cells": cells_of(W64), "dtype": "f64",
+                 "value": r64["value"], "ms_per_step": r64["ms_per_step"], "steps": r64["steps"],
+                 "pflow_ms": r64["pflow_ms"], "pflow_tflops": achieved64,
+                 "pflow_frac_of_measured_fp64_fma": (achieved64 / fma64) if fma64 else None,
+                 "fp32_mixed_same_workload": {"value": r64_32["value"],
+                                              "ms_per_step": r64_32["ms_per_step"],
+                                              "steps": r64_32["steps"]},
+                 "fp32_over_fp64": r64_32["value"] / r64["value"]},
+        "stationarity": stat,
         "lpc1": lpc1,
         "serving": serving,
         "roofline": {"kernel": "k_theta_xs (P(dt): four Horner stages of Theta^T per x point, "
                                "table form)",
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "peak_source": f"derived: {num_sms} SMs x 128 FP32 lanes x 2 x max SM clock",
                      "measured_fma_peak_tflops": fma32,
                      "frac_of_measured_fma_peak": (achieved / fma32) if fma32 else None,
                      "measured_packed_f32x2_fma_tflops": fma32x2,
                      "ms_per_launch": r32["pflow_ms"],
                      "flops_per_launch": flops_launch,
                      "traffic": (tr["dram_bytes_per_launch"] * cells / tr["cells"]) if tr else None},
-        "e2e": r32["e2e"],
+        "e2e": e2e,
         "gpu_launches": 7 * args.steps,
         "clocks": clocks,
         "cpu_baseline": base,
@@ -465,34 +682,6 @@ def run_chasm(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
-
-
-def accuracy_check(torch, ch, stream, steps):
-    """Both forms from the same 1s initial data for `steps` steps: relative L2 of the FP32-mixed
-    result against the FP64 result (the FP64 form is itself pinned to the FP64 oracle) and the
-    relative mass drift of each."""
-    W = WORKLOAD
-    out = {}
-    with torch.cuda.stream(stream):
-        for name, prec, dtp in (("fp64", ch.FP64, torch.float64), ("fp32", ch.FP32_MIXED, torch.float32)):
-            s = make_solver(ch, prec, stream)
-            f = torch.empty((W["nx"],) * 3 + (W["nk"],) * 3, device="cuda", dtype=dtp)
-            s.init_hydrogen_1s(f, n_y=W["n_y"])
-            m0, _ = s.moments(f)
-            s.step(f, W["dt"], steps)
-            m1, _ = s.moments(f)
-            out[name] = (f, (m1 - m0) / m0, m1)
-            s.close()
-        a, b = out["fp32"][0].double(), out["fp64"][0]
-        rel = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
-        res = {"steps": steps, "rel_l2_fp32_vs_fp64": rel, "tolerance": 1e-5,
-               "mass_rel_diff_fp32_vs_fp64": (out["fp32"][2] - out["fp64"][2]) / out["fp64"][2],
-               "mass_drift_fp32": out["fp32"][1], "mass_drift_fp64": out["fp64"][1],
-               "note": "the FP64 form is pinned to the FP64 oracle at <= 1e-12"}
-        del a, b, out
-    torch.cuda.synchronize()
-    torch.cuda.empty_cache()
-    return res
 
 
 def serving_specs(seed, n_req, nx_choices, nk_choices, steps, precisions, L=12.0, lk=4.0):
@@ -553,6 +742,25 @@ def run_serving(ch, n_req, rate, seed, nx_choices, nk_choices, steps, precisions
     return out
 
 
+def serving_both(ch, n_req, rate, steps, seed=2205, budget=150 << 30, max_slots=8, spl=5):
+    """The same seeded request stream (grids {16,24,32}^3 x {16,32}^3, 1-2 protons, an electron
+    packet, `steps` steps each, the same Poisson arrival times) served once in each form: the
+    FP32-mixed form's latency percentiles next to the FP64 form's on the same GPU."""
+    out = {}
+    for name, prec in (("fp32_mixed", ch.FP32_MIXED), ("fp64", ch.FP64)):
+        out[name] = run_serving(ch, n_req=n_req, rate=rate, seed=seed, nx_choices=(16, 24, 32),
+                                nk_choices=(16, 32), steps=steps, precisions=(prec,),
+                                budget=budget, max_slots=max_slots, spl=spl)
+        r = out[name]
+        r["mean_request_cell_updates"] = r["cell_updates_per_s"] * r["wall_s"] / n_req
+    out["p99_ms_fp32_mixed_vs_fp64"] = [out["fp32_mixed"]["p99_ms"], out["fp64"]["p99_ms"]]
+    out["sample"] = (f"{n_req} requests of the serving stream (grids {{16,24,32}}^3 x {{16,32}}^3, "
+                     f"1-2 protons in [-2,2]^3, packet centre in [-4,4]^3, momentum in "
+                     f"[-1.5,1.5]^3, {steps[0]}-{steps[1]} steps at dt 0.025, HBM budget 150 GB, "
+                     f"{max_slots} slots), Poisson {rate}/s, the same stream in each form")
+    return out
+
+
 def latency_percentile(sorted_ms, q):
     """Nearest-rank percentile of an ascending list."""
     return sorted_ms[min(len(sorted_ms) - 1, max(0, int(math.ceil(q * len(sorted_ms))) - 1))]
@@ -581,24 +789,20 @@ def serving_stats(rows, wall):
 
 def run_serve_mode(args):
     """The serving workload: 64 requests, grids {16,24,32}^3 x {16,32}^3, 10-100 steps, HBM budget
-    150 GB, Poisson arrivals at --rate per second, in FP32-mixed.  The FP64 form runs on the FP64
-    pipe (1/64 of the FP32 rate on this GPU; about 1.9 s per 32^3 x 32^3 step), so the stream
-    that mixes both precisions is a bounded sample: --serve-mixed-requests requests (default 16)
-    with at most 30 steps each."""
-    import torch
+    150 GB, Poisson arrivals at --rate per second, in FP32-mixed; and the first
+    --serve-fp64-requests requests of the same stream with at most 30 steps served in each form
+    (the FP64 form runs on the FP64 pipe, about 30 times slower per cell on this GPU)."""
     import paper_2205_02380_gb300 as ch
     ch.chasm.lib()
     out = {"metric": "serving latency and throughput", "unit": "ms / cell-updates/s"}
-    plan = (("fp32", (ch.FP32_MIXED,), args.serve_requests, args.serve_max_steps),
-            ("mixed", (ch.FP32_MIXED, ch.FP64), args.serve_mixed_requests, 30))
-    for name, precs, n_req, max_steps in plan:
-        if args.serve_precisions and name not in args.serve_precisions.split(","):
-            continue
-        out[name] = run_serving(ch, n_req=n_req, rate=args.rate, seed=2205,
-                                nx_choices=(16, 24, 32), nk_choices=(16, 32),
-                                steps=(10, max_steps), precisions=precs,
-                                budget=150 << 30, max_slots=args.slots, spl=5)
-        out[name]["sample"] = f"{n_req} requests, steps 10-{max_steps}"
+    out["fp32_stream"] = run_serving(ch, n_req=args.serve_requests, rate=args.rate, seed=2205,
+                                     nx_choices=(16, 24, 32), nk_choices=(16, 32),
+                                     steps=(10, args.serve_max_steps), precisions=(ch.FP32_MIXED,),
+                                     budget=150 << 30, max_slots=args.slots, spl=5)
+    out["fp32_stream"]["sample"] = f"{args.serve_requests} requests, steps 10-{args.serve_max_steps}"
+    if args.serve_fp64_requests > 0:
+        out["both_forms"] = serving_both(ch, n_req=args.serve_fp64_requests, rate=args.fp64_rate,
+                                         steps=(10, 30), max_slots=args.slots)
     print(json.dumps(out), flush=True)
 
 
@@ -610,7 +814,7 @@ def run_kernels(args):
     clock around a synchronised loop, so their figure includes the call's return latency."""
     import torch
     import paper_2205_02380_gb300 as ch
-    W = WORKLOAD
+    W = WORKLOADS[STATIONARITY]
     n, nk = W["nx"], W["nk"]
     fb = n ** 3 * nk ** 3 * 4
     peak = measured_hbm_gbs()
@@ -645,9 +849,9 @@ def run_kernels(args):
 
     shape = (n,) * 3 + (nk,) * 3
     with torch.cuda.stream(stream):
-        s = make_solver(ch, ch.FP32_MIXED, stream)
+        s = make_solver(ch, W, ch.FP32_MIXED, stream)
         f = torch.empty(shape, device="cuda", dtype=torch.float32)
-        s.init_hydrogen_1s(f, n_y=W["n_y"])
+        init_f(s, W, f)
         put("mass_energy", "k_moments", wall_ms(lambda: s.moments(f), 5), fb, "wall")
         for j in range(3):
             put(f"reduced_wigner_{j}", "k_diag_kpart + k_diag_wigner",
@@ -671,50 +875,56 @@ def run_kernels(args):
 
 
 def run_profile(args):
-    """FP32 form only: init, W warm-up steps and K steps, nothing else (for ncu)."""
+    """FP32 form only on --workload (default the headline one, --nx overrides N_x): init, W
+    warm-up steps and K steps, nothing else (for ncu)."""
     import torch
     import paper_2205_02380_gb300 as ch
-    W = WORKLOAD
+    W = WORKLOADS[args.workload]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        s = make_solver(ch, ch.FP32_MIXED, stream)
-        f = torch.empty((W["nx"],) * 3 + (W["nk"],) * 3, device="cuda", dtype=torch.float32)
-        s.init_hydrogen_1s(f, n_y=W["n_y"])
+        s = make_solver(ch, W, ch.FP32_MIXED, stream)
+        f = new_f(torch, W, torch.float32)
+        init_f(s, W, f)
         ms = time_steps(torch, s, f, W["dt"], args.steps, args.warmup, stream, None)
         s.close()
-    print(json.dumps({"profile_ms_per_step": ms / max(1, args.steps), "nx": W["nx"]}))
+    print(json.dumps({"profile_ms_per_step": ms / max(1, args.steps), "workload": W["name"]}))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="chasm", choices=["chasm", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--stat-steps", type=int, default=40,
+                    help="steps of the hydrogen 1s stationarity run in both forms (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", action="store_true")
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS))
     ap.add_argument("--profile", action="store_true",
                     help="FP32 timed steps only (no FP64, e2e, baseline or clocks): for ncu captures")
     ap.add_argument("--nx", type=int, default=None, help="override N_x (profiling on smaller cases)")
-    ap.add_argument("--acc-steps", type=int, default=4)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-lpc1", action="store_true")
+    ap.add_argument("--bench-serve-requests", type=int, default=8)
+    ap.add_argument("--bench-serve-rate", type=float, default=2.0)
     ap.add_argument("--kernels", action="store_true",
                     help="bandwidth of the reduction, diagnostic and quadratic-potential kernels")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--rate", type=float, default=5.0)
+    ap.add_argument("--fp64-rate", type=float, default=0.2)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-max-steps", type=int, default=100)
-    ap.add_argument("--serve-mixed-requests", type=int, default=16)
-    ap.add_argument("--serve-precisions", default="")
-    ap.add_argument("--sample-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-fp64-requests", type=int, default=16)
     args = ap.parse_args()
     if args.nx:
-        WORKLOAD["nx"] = args.nx
-        WORKLOAD["name"] = WORKLOAD["name"].replace("32^3x32^3", f"{args.nx}^3x32^3")
+        W = WORKLOADS[args.workload]
+        old = f"{W['nx']}^3x"
+        W["nx"] = args.nx
+        W["name"] = W["name"].replace(old, f"{args.nx}^3x")
     if args.profile:
         run_profile(args)
         return
@@ -725,7 +935,7 @@ def main():
         run_serve_mode(args)
         return
     if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.sample_seconds)))
+        print(json.dumps(cpu_baseline_run(args.workload)))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -116,3 +116,55 @@ def test_run_serving_end_to_end_with_a_fake_server():
     specs = bench.serving_specs(7, 6, (16,), (16,), (10, 12), (0, 1))
     if len({s["precision"] for s in specs}) > 1:
         assert sum(b["requests"] for b in out["by_precision"].values()) == 6
+
+
+def test_deviation_metrics_match_the_oracle_error_metrics():
+    """The bench reduces eps_inf and eps_2 (Sec. 5) on the device; on CPU tensors its helper
+    gives the pinned oracle's values."""
+    import numpy as np
+    import bench
+    from oracle import chasm_oracle as O
+    prob = O.Problem(nx=(5, 4, 6), nk=4, x_lo=(-2.0, -1.0, -3.0), x_hi=(2.0, 1.4, 2.0), lk=1.4)
+    rng = np.random.default_rng(11)
+    a = rng.standard_normal(prob.shape)
+    b = a + 1e-3 * rng.standard_normal(prob.shape)
+    got = bench.deviation_metrics(torch, torch.from_numpy(a).float(), torch.from_numpy(b),
+                                  O.cell_volume(prob))
+    ref = O.errors(b, a.astype(np.float32).astype(np.float64), prob)
+    assert got == pytest.approx(ref, rel=1e-12)
+
+
+def test_serving_both_forms_serve_the_same_stream():
+    """serving_both submits the same requests (grid, steps, potential, packet) in each form."""
+    import types
+    import bench
+
+    seen = {0: [], 1: []}
+
+    class FakeServer:
+        def __init__(self, budget, max_slots, steps_per_launch, queue_capacity):
+            self.reqs = []
+
+        def submit(self, req):
+            self.reqs.append(req)
+            seen[req["precision"]].append({k: v for k, v in req.items() if k != "precision"})
+            return len(self.reqs) - 1
+
+        def wait(self, ticket, timeout):
+            r = self.reqs[ticket]
+            return types.SimpleNamespace(latency_ms=10.0 + ticket + 100 * r["precision"],
+                                         queue_ms=0.0, cells=r["cells"], nsteps=r["nsteps"],
+                                         status=0)
+
+        def close(self):
+            pass
+
+    def make_request(nx, nk, lo, hi, lk, dt, nsteps, nuclei, packets, precision):
+        return {"cells": nx ** 3 * nk ** 3, "nsteps": nsteps, "precision": precision,
+                "nuclei": nuclei, "packets": packets}
+
+    ch = types.SimpleNamespace(Server=FakeServer, make_request=make_request, FP32_MIXED=0, FP64=1)
+    out = bench.serving_both(ch, n_req=5, rate=1e6, steps=(10, 15))
+    assert seen[0] == seen[1] and len(seen[0]) == 5
+    assert out["fp32_mixed"]["requests"] == out["fp64"]["requests"] == 5
+    assert out["p99_ms_fp32_mixed_vs_fp64"] == [14.0, 114.0]
