@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libchasm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "k_advect.cu", "k_theta.cu", "k_theta_xs.cu", "k_xsym.cu", "k_symbol.cu",
+SOURCES = ["capi.cu", "k_advect.cu", "k_theta.cu", "k_theta_xs.cu", "k_theta_pk.cu", "k_xsym.cu", "k_symbol.cu",
            "k_misc.cu", "k_lpc1.cu", "k_diag.cu", "k_peak.cu", "server.cu",
            "noalloc.cu"]
 
@@ -47,6 +47,7 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(CSRC, "internal.hpp"), os.path.join(CSRC, "fft_reg.cuh"),
+                   os.path.join(CSRC, "fft_pk.cuh"),
                    os.path.join(HERE, "..", "include", "chasm.h")]
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) > max(os.path.getmtime(p) for p in deps)):

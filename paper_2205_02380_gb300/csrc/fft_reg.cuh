@@ -298,45 +298,13 @@ struct VLayout {
   static constexpr int D = N >= 16 ? 8 : N / 2;   // lane h keeps the elements m with (m / D) % 2 == h
 };
 
-// Rows of V for the split-half combine: rows r >= N/2 start PAD elements (64 bytes) later, so that
-// the two lanes of a pair, which write rows k and k + N/2 of the same column, hit different banks
-// (N/2 VR is a multiple of the 16 banks of 8-byte elements for N = 32).
-template <typename T, int N, bool SPLIT>
+// Rows of the group's slab buffer V: N rows of stride VR.
+template <typename T, int N>
 struct VRows {
-  static constexpr int PAD = SPLIT ? 64 / (int)sizeof(cpx<T>) : 0;
-  static constexpr int SIZE = N * VLayout<N>::VR + PAD;   // elements per group buffer
-  __host__ __device__ static constexpr int off(int r) { return r * VLayout<N>::VR + (r >= N / 2 ? PAD : 0); }
+  static constexpr int SIZE = N * VLayout<N>::VR;   // elements per group buffer
+  __host__ __device__ static constexpr int off(int r) { return r * VLayout<N>::VR; }
 };
 
-// Conjugate twist of a vector whose register n holds index (n + N/2) mod N (the output of an
-// inverse transform whose input was modulated by (-1)^j): x_n *= e^{+i pi idx / N}.
-template <typename T, int N>
-__device__ __forceinline__ void twist_conj_shifted(T (&re)[N], T (&im)[N]) {
-#pragma unroll
-  for (int n = 0; n < N; ++n) {
-    const int idx = (n + N / 2) % N;
-    if (idx == 0) continue;
-    const int k64 = idx * (32 / N);
-    const T c = tw_cos<T>(k64), s = tw_sin<T>(k64);
-    const T a = re[n], b = im[n];
-    re[n] = a * c - b * s;
-    im[n] = a * s + b * c;
-  }
-}
-
-// Split-half combine: lane h of a pair holds in register k the element k + h N/2 (lane 0: natural
-// order; lane 1: shifted by N/2), so r_k = mine_k + partner's_{k + N/2} is output element k + h N/2
-// for k < N/2, with no selects.  dst points at the lane's first output element.
-template <typename T, int N>
-__device__ __forceinline__ void split_combine_store(const T (&re)[N], const T (&im)[N], cpx<T>* dst,
-                                                    int stride) {
-#pragma unroll
-  for (int k = 0; k < N / 2; ++k) {
-    const T rre = __shfl_xor_sync(0xffffffffu, re[k + N / 2], 1);
-    const T rim = __shfl_xor_sync(0xffffffffu, im[k + N / 2], 1);
-    dst[k * stride] = {re[k] + rre, im[k] + rim};
-  }
-}
 // r = mine + partner's (parity partials of the same output vector); lane h stores the elements m
 // with (m / D) % 2 == h of r at dst[m * stride], so the two lanes of a pair write rows D apart.
 template <typename T, int N, bool GLOBAL = false>
@@ -391,18 +359,12 @@ __device__ __forceinline__ void pair_combine_store_row(const float (&re)[N], con
 // N x (2N + 1) complex buffer.  th is the slab of the symbol (parity-major [s1][s2], row length
 // 2N): real (the spectrum is multiplied by th) or, with IMAG, the imaginary part of a purely
 // imaginary symbol (the spectrum is multiplied by i th).
-//  With SPLIT (IMAG, single precision, global spectrum rows; the symbol table carries the signs of
-//  xs_split) the column inverse transforms of lane 1 (B2) come out shifted by N/2 and the pair
-//  combine keeps contiguous halves of the column; V has the rows of VRows<T, N, true>.  (B3 keeps
-//  the interleaved combine: split halves of a global row would touch twice the cache lines per
-//  store.)
-template <typename T, int N, int GS, int SR, bool GLOBAL, bool IMAG = false, bool SPLIT = false>
+template <typename T, int N, int GS, int SR, bool GLOBAL, bool IMAG = false>
 __device__ __forceinline__ void slab_conv(cpx<T>* Gs, cpx<T>* V, const T* __restrict__ th, int tg,
                                           int grp, uint64_t pol) {
-  static_assert(!SPLIT || (IMAG && GLOBAL && sizeof(T) == 4), "split combine: table form, FP32 rows");
   constexpr int L = 2 * N;
   using VL = VLayout<N>;
-  using VW = VRows<T, N, SPLIT>;
+  using VW = VRows<T, N>;
   const int h = tg & 1, row = tg >> 1;
   const int vrow = VW::off(row);
   {  // B1: forward along k2 of row k1 = row, parity h
@@ -459,13 +421,8 @@ __device__ __forceinline__ void slab_conv(cpx<T>* Gs, cpx<T>* V, const T* __rest
       }
     }
     fft<T, N, true>(re, im);
-    if constexpr (SPLIT) {   // lane h writes rows [h N/2, (h + 1) N/2) of column c
-      if (h) twist_conj_shifted<T, N>(re, im);
-      split_combine_store<T, N>(re, im, V + vc + (h ? VW::off(N / 2) : 0), VL::VR);
-    } else {
-      if (h) twist<T, N, true>(re, im);
-      pair_combine_store<T, N>(re, im, h, V + vc, VL::VR);   // column c is read by this pair only
-    }
+    if (h) twist<T, N, true>(re, im);
+    pair_combine_store<T, N>(re, im, h, V + vc, VL::VR);   // column c is read by this pair only
   }
   group_sync<GS>(grp);
   {  // B3: inverse along k2 of row n1 = row, parity h; result back into the slab

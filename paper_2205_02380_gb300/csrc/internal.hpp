@@ -88,12 +88,14 @@ cudaError_t measure_fma_peak_f32x2(double* tflops);
 // the per-x symbol table (k_xsym.cu), [nxp][N][2N][2N] in the storage type; needs H.d_T
 size_t xs_table_bytes(int nk, int64_t nxp, size_t elt);
 cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s);
-// Split-half combine of the table-form slab phase (single precision, N_k = 32): the symbol table
-// carries the sign pattern (-1)^jj on the parity-1 runs, which shifts the parity-1 lane's inverse
-// transforms along k1 by N/2 so that each lane of a pair keeps a contiguous half of the column
-// without selects (k_xsym.cu writes the signs, fft_reg.cuh uses them).
-template <typename T, int N>
-__host__ __device__ constexpr bool xs_split() { return sizeof(T) == 4 && N == 32; }
+// Packed single-precision variant of the table-form P(dt) kernel (k_theta_pk.cu), used for
+// FP32-mixed handles with N_k = 16 or 32: its symbol table has the layout
+// [x][j][xi1 / 4][xi2][xi1 % 4] (k_xsym.cu writes it), the other cases [x][j][s1][s2]
+// parity-major.
+__host__ __device__ constexpr bool xs_packed(bool fp64, int nk) { return !fp64 && (nk == 16 || nk == 32); }
+void theta_pk_plan(int nk, int64_t nxp, int num_sms, ThetaPlan* plan);
+cudaError_t launch_theta_pk(const Handle& H, const void* in, const void* base, void* out, int nst,
+                            const double* coef, cudaStream_t s, const XsExtra& x);
 
 constexpr size_t kXsAutoMaxBytes = (size_t)64 << 30;
 

@@ -1,4 +1,5 @@
-// Coulomb operator and P-flow in the real form with a per-x symbol table (Sec. 4).
+// Coulomb operator and P-flow in the real form with a per-x symbol table (Sec. 4): FP64 and
+// N_k = 8 (single precision with N_k = 16 or 32 runs the packed kernel of k_theta_pk.cu).
 //
 // For one x point, Theta^T is a real linear convolution over the k-grid:
 //   Theta^T[u]_p = sum_q S_{p-q}(x) u_q,
@@ -21,7 +22,6 @@
 // Per x point (one CTA, persistent loop over x points):
 //   Phase A   N^2 lines along k3: twist, FFT_N -> G[j][k1][k2]
 //   Phase B   N slabs j: the 2-D padded convolution in (k1, k2) (slab_conv), spectrum times i sigma
-//             (single precision, N = 32: the column combines split in halves, xs_split)
 //   Phase CA  N^2 lines: inverse FFT_N along k3, conjugate twist, real part = Theta line;
 //             v = base + c_s Theta.  After the last stage v is written out; otherwise the same
 //             thread twists and transforms v in place of the next stage's Phase A (same lines,
@@ -62,8 +62,7 @@ struct XsCfg {
   static constexpr int SR = GSM ? N + 1 : N;   // spectrum row stride (padded in shared memory)
   static constexpr int SLAB = N * SR;
   static_assert(NT % GS == 0 && (GS <= 32 || NG <= 15), "slab groups must tile the CTA");
-  static constexpr bool SPLIT = xs_split<T, N>();
-  static constexpr int VSIZE = VRows<T, N, SPLIT>::SIZE;   // group slab buffer, elements
+  static constexpr int VSIZE = VRows<T, N>::SIZE;   // group slab buffer, elements
   static constexpr size_t smem_cpx = (size_t)NG * VSIZE + (GSM ? (size_t)N * SLAB : 0);
   static constexpr size_t smem_bytes = smem_cpx * sizeof(cpx<T>);
 };
@@ -231,7 +230,7 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
           const int64_t xn = s + NG < N || st + 1 < p.nst ? xp : xp + gridDim.x;
           if (xn < p.nxp) bulk_prefetch_l2(p.sig + (xn * N + sn) * (int64_t)(L * L), L * L * sizeof(T));
         }
-        slab_conv<T, N, GS, SR, !GSM, true, C::SPLIT>(G + (size_t)s * SLAB, V,
+        slab_conv<T, N, GS, SR, !GSM, true>(G + (size_t)s * SLAB, V,
                                             p.sig + (xp * N + s) * (int64_t)(L * L), tg, grp, pol);
       }
       __syncthreads();
@@ -315,30 +314,33 @@ cudaError_t launch_xs_tn(const Handle& H, const void* in, const void* base, void
 cudaError_t launch_theta_xs(const Handle& H, const void* in, const void* base, void* out, int nst,
                             const double* coef, cudaStream_t s, const XsExtra& x) {
   if (nst < 1 || nst > 4 || !H.d_sig) return cudaErrorInvalidValue;
+  if (xs_packed(H.fp64, H.g.nk)) return launch_theta_pk(H, in, base, out, nst, coef, s, x);
   switch (H.g.nk) {
     case 8:
       return H.fp64 ? launch_xs_tn<double, 8>(H, in, base, out, nst, coef, x, s)
                     : launch_xs_tn<float, 8>(H, in, base, out, nst, coef, x, s);
     case 16:
-      return H.fp64 ? launch_xs_tn<double, 16>(H, in, base, out, nst, coef, x, s)
-                    : launch_xs_tn<float, 16>(H, in, base, out, nst, coef, x, s);
+      return H.fp64 ? launch_xs_tn<double, 16>(H, in, base, out, nst, coef, x, s) : cudaErrorInvalidValue;
     case 32:
-      return H.fp64 ? launch_xs_tn<double, 32>(H, in, base, out, nst, coef, x, s)
-                    : launch_xs_tn<float, 32>(H, in, base, out, nst, coef, x, s);
+      return H.fp64 ? launch_xs_tn<double, 32>(H, in, base, out, nst, coef, x, s) : cudaErrorInvalidValue;
   }
   return cudaErrorInvalidValue;
 }
 
 void theta_xs_plan(int nk, bool fp64, int64_t nxp, int num_sms, ThetaPlan* pl) {
+  if (xs_packed(fp64, nk)) {
+    theta_pk_plan(nk, nxp, num_sms, pl);
+    return;
+  }
   switch (nk) {
     case 8:
       fp64 ? plan_xs_tn<double, 8>(nxp, num_sms, pl) : plan_xs_tn<float, 8>(nxp, num_sms, pl);
       return;
     case 16:
-      fp64 ? plan_xs_tn<double, 16>(nxp, num_sms, pl) : plan_xs_tn<float, 16>(nxp, num_sms, pl);
+      if (fp64) plan_xs_tn<double, 16>(nxp, num_sms, pl);
       return;
     case 32:
-      fp64 ? plan_xs_tn<double, 32>(nxp, num_sms, pl) : plan_xs_tn<float, 32>(nxp, num_sms, pl);
+      if (fp64) plan_xs_tn<double, 32>(nxp, num_sms, pl);
       return;
   }
   pl->cluster = 0;

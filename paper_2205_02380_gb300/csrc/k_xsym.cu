@@ -13,9 +13,9 @@
 // tables and the first two contractions are FP64; the last runs in the storage precision (FP32
 // for the mixed form: its rounding adds about 1e-7 relative to Theta) with FP64 inputs rounded
 // once.  The table is written as [x][j][s1][s2], s = (xi mod 2) N + xi / 2 per dimension (the
-// parity-major order of the slab phase).  For the split-half combine (xs_split: single precision,
-// N = 32) an entry with odd xi1 is multiplied by (-1)^(xi1 / 2): the modulation that shifts the
-// slab phase's parity-1 inverse transforms along k1 by N/2.
+// parity-major order of the slab phase of k_theta_xs.cu), or, for the packed single-precision
+// kernel (xs_packed: k_theta_pk.cu), as [x][j][xi1 / 4][xi2][xi1 % 4] in natural frequency order
+// (a lane of its column pass reads the four values of one 16-byte quad).
 #include <cmath>
 
 #include "internal.hpp"
@@ -154,10 +154,13 @@ __global__ void __launch_bounds__(256) k_xs_table(const double* __restrict__ C1,
         for (int m = 0; m < N; ++m) acc = fma(c1s[0][xi1][m], r[0][m], acc);
 #pragma unroll
         for (int m = 0; m < N; ++m) acc = fma(c1s[1][xi1][m], r[1][m], acc);
-        const int s1 = (xi1 & 1) * N + xi1 / 2;
-        T* dst = out + ((int64_t)j * L + s1) * L + s2;
-        if constexpr (xs_split<T, N>()) {   // (-1)^jj on parity-1 runs
-          if ((xi1 & 1) && ((xi1 / 2) & 1)) acc = -acc;
+        T* dst;
+        if constexpr (xs_packed(sizeof(T) == 8, N)) {
+          const int xi2 = 2 * (s2 % N) + s2 / N;
+          dst = out + (((int64_t)j * (L / 4) + xi1 / 4) * L + xi2) * 4 + (xi1 & 3);
+        } else {
+          const int s1 = (xi1 & 1) * N + xi1 / 2;
+          dst = out + ((int64_t)j * L + s1) * L + s2;
         }
         *dst = A == 0 ? (T)acc : (T)((AT)*dst + acc);
       }
