@@ -18,9 +18,10 @@
 //     the end: Re[e^{i phi} i y] = -(sin phi Re y + cos phi Im y), the sign folded into the
 //     Horner coefficient.
 // Data layouts (floats):
-//   spectrum G[j][k1][m] (float4) = (Re z_{2m}, Re z_{2m+1}, Im z_{2m}, Im z_{2m+1}), z the k3
-//     spectrum of the line pair (k1, k2 = 2m, 2m + 1) at frequency j: a row k1 of slab j holds
-//     the N values along k2 as N/2 such quads;
+//   spectrum G[j][m][k1] (float4) = (Re z_{2m}, Re z_{2m+1}, Im z_{2m}, Im z_{2m+1}), z the k3
+//     spectrum of the line pair (k1, k2 = 2m, 2m + 1) at frequency j: row k1 of slab j holds the
+//     N values along k2 as the N/2 quads m, N quads apart (the lanes of a row pass, one row each,
+//     touch N consecutive quads per access);
 //   slab buffer V[row][jj] (float4, one buffer of N rows per slab, row stride 4N + 4 floats) =
 //     (Re E_jj, Re O_jj, Im E_jj, Im O_jj) for the frequency pair (2 jj, 2 jj + 1), halves
 //     swapped when jj & 8 (so the column accesses of the second pass are free of bank conflicts);
@@ -48,7 +49,7 @@ struct PkParams {
   const float* sig;    // [nxp][N][L/4][L][4] symbol table
   int nst;             // stages, 1..4
   float ncoef[4];      // -c_s per stage (the sign of the deferred factor i)
-  float4* G;           // per-CTA spectrum scratch [N][N][N/2] when it is not in shared memory
+  float4* G;           // per-CTA spectrum scratch [N][N/2][N] when it is not in shared memory
 };
 
 template <int N>
@@ -182,7 +183,7 @@ __device__ __forceinline__ void slab_rows_forward(const float4* g, float* vrow, 
   pc x[N];
 #pragma unroll
   for (int mm = 0; mm < N / 2; ++mm) {
-    const float4 v = g_load<GSM>(g + mm, pol);
+    const float4 v = g_load<GSM>(g + mm * N, pol);
     x[2 * mm] = {f2(v.x, 0.f), f2(v.z, 0.f)};
     x[2 * mm + 1] = {f2(v.y, 0.f), f2(v.w, 0.f)};
   }
@@ -234,7 +235,7 @@ __device__ __forceinline__ void slab_rows_inverse(float4* g, const float* vrow, 
     constexpr int mm = decltype(M)::value;
     const float2 a = join_pair<N, 2 * mm>(x[2 * mm]);
     const float2 b = join_pair<N, 2 * mm + 1>(x[2 * mm + 1]);
-    g_store<GSM>(g + mm, make_float4(a.x, b.x, a.y, b.y), pol);
+    g_store<GSM>(g + mm * N, make_float4(a.x, b.x, a.y, b.y), pol);
   });
 }
 
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
   for (int64_t xp = blockIdx.x; xp < p.nxp; xp += gridDim.x) {
     // ---- Phase A: k3 forward of the stage-0 input ----
     for (int pr = tid; pr < NP; pr += NT) {
-      const int k1 = pr / (N / 2), m = pr % (N / 2);
+      const int k1 = pr % N, m = pr / N;
       const size_t off = (size_t)xp * N3 + ((size_t)k1 * N + 2 * m) * N;
       float a[N], b[N];
       load_pair<N>(p.in + off, a, b);
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
           b[n] = fmaf(p.cin2, b2[n], b[n]);
         }
       }
-      k3_forward<N, GSM>(a, b, G + (size_t)k1 * (N / 2) + m, pol);
+      k3_forward<N, GSM>(a, b, G + (size_t)m * N + k1, pol);
     }
     __syncthreads();
 
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
         }
         float* Vs = Vw + sub * N * RS;
         float4* gs = G + (size_t)(s0 + sub) * SQ;
-        slab_rows_forward<N, GSM>(gs + (size_t)r * (N / 2), Vs + r * RS, pol);
+        slab_rows_forward<N, GSM>(gs + r, Vs + r * RS, pol);
         __syncwarp();
 #pragma unroll 1
         for (int rnd = 0; rnd < 2; ++rnd) {
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
           slab_column<N>(Vw + sc * N * RS, c, sg, spol);
         }
         __syncwarp();
-        slab_rows_inverse<N, GSM>(gs + (size_t)r * (N / 2), Vs + r * RS, pol);
+        slab_rows_inverse<N, GSM>(gs + r, Vs + r * RS, pol);
         __syncwarp();
       }
       __syncthreads();
@@ -306,9 +307,9 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
 
       // ---- Phase CA: k3 inverse, Theta, Horner update; the next stage's k3 forward ----
       for (int pr = tid; pr < NP; pr += NT) {
-        const int k1 = pr / (N / 2), m = pr % (N / 2);
+        const int k1 = pr % N, m = pr / N;
         const size_t off = (size_t)xp * N3 + ((size_t)k1 * N + 2 * m) * N;
-        float4* g = G + (size_t)k1 * (N / 2) + m;
+        float4* g = G + (size_t)m * N + k1;
         pc y[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
