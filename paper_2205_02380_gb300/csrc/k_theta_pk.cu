@@ -254,26 +254,29 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
   const uint64_t spol = l2_stream_policy();
   const int sub = lane / N, r = lane % N;
 
-  for (int64_t xp = blockIdx.x; xp < p.nxp; xp += gridDim.x) {
-    // ---- Phase A: k3 forward of the stage-0 input ----
-    for (int pr = tid; pr < NP; pr += NT) {
-      const int k1 = pr % N, m = pr / N;
-      const size_t off = (size_t)xp * N3 + ((size_t)k1 * N + 2 * m) * N;
-      float a[N], b[N];
-      load_pair<N>(p.in + off, a, b);
-      if (X2 && p.in2) {   // u_0 = in + cin2 in2 (the LPC1 predictor)
-        float a2[N], b2[N];
-        load_pair<N>(p.in2 + off, a2, b2);
+  // Phase A for line pair pr of x point xq: k3 forward of the stage-0 input
+  auto phase_a = [&](int64_t xq, int pr) {
+    const int k1 = pr % N, m = pr / N;
+    const size_t off = (size_t)xq * N3 + ((size_t)k1 * N + 2 * m) * N;
+    float a[N], b[N];
+    load_pair<N>(p.in + off, a, b);
+    if (X2 && p.in2) {   // u_0 = in + cin2 in2 (the LPC1 predictor)
+      float a2[N], b2[N];
+      load_pair<N>(p.in2 + off, a2, b2);
 #pragma unroll
-        for (int n = 0; n < N; ++n) {
-          a[n] = fmaf(p.cin2, a2[n], a[n]);
-          b[n] = fmaf(p.cin2, b2[n], b[n]);
-        }
+      for (int n = 0; n < N; ++n) {
+        a[n] = fmaf(p.cin2, a2[n], a[n]);
+        b[n] = fmaf(p.cin2, b2[n], b[n]);
       }
-      k3_forward<N, GSM>(a, b, G + (size_t)m * N + k1, pol);
     }
-    __syncthreads();
+    k3_forward<N, GSM>(a, b, G + (size_t)m * N + k1, pol);
+  };
+  if (blockIdx.x < p.nxp) {
+    for (int pr = tid; pr < NP; pr += NT) phase_a(blockIdx.x, pr);
+  }
+  __syncthreads();
 
+  for (int64_t xp = blockIdx.x; xp < p.nxp; xp += gridDim.x) {
     for (int st = 0; st < p.nst; ++st) {
       // ---- Phase B: one warp per slab group ----
       for (int s0 = warp * SPW; s0 < N; s0 += NW * SPW) {
@@ -340,9 +343,12 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
           a[n] = fmaf(nc, th.x, a[n]);
           b[n] = fmaf(nc, th.y, b[n]);
         });
-        if (last)
+        if (last) {
           store_pair<N>(p.out + off, a, b);
-        else
+          // this thread alone used these spectrum columns: the next x point's Phase A for the
+          // same line pair writes them without a barrier
+          if (xp + gridDim.x < p.nxp) phase_a(xp + gridDim.x, pr);
+        } else
           k3_forward<N, GSM>(a, b, g, pol);
       }
       __syncthreads();
