@@ -13,126 +13,93 @@ constexpr int kMomThreads = 256;
 // ---------------------------------------------------------------------------------------------
 // Mass and energy (diagnostics of Sec. 5): per x point, S0 = sum_k f and S2 = sum_k |k|^2 f;
 // mass += S0, energy += (hbar^2/2m) dk^2 S2' + V(x) S0 where S2' uses integer |j - N/2|^2.
-// Each block owns a fixed set of x points and reduces them in a fixed order; a second kernel
-// adds the block partials in a fixed order, so the result is bitwise reproducible.
+// Every thread accumulates its own elements of the block's x points (V(x) S0 is linear in the
+// thread's partial of S0, so no per-x-point reduction is needed); one block reduction at the end
+// and a second kernel that adds the block partials in a fixed order make the result bitwise
+// reproducible (the grid size is fixed).
 // ---------------------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* __restrict__ out) {
+  __shared__ double red[NV][kMomThreads / 32];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < NV; ++c)
+    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) red[c][tid >> 5] = v[c];
+  __syncthreads();
+  if (tid == 0)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      double a = 0.0;
+      for (int w = 0; w < kMomThreads / 32; ++w) a += red[c][w];
+      out[(int64_t)NV * blockIdx.x + c] = a;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kMomThreads) k_moments(const T* __restrict__ f, int64_t nxp,
                                                          int nk, const double* __restrict__ vx,
                                                          double* __restrict__ partials) {
-  __shared__ double red[2][kMomThreads / 32];
-  const int tid = threadIdx.x;
   const int kvol = nk * nk * nk;
-  double bm = 0.0, bk = 0.0, bv = 0.0;   // block accumulators (thread 0)
+  double acc[3] = {0.0, 0.0, 0.0};   // sum f, sum |j - N/2|^2 f, sum V(x) f
   for (int64_t xp = blockIdx.x; xp < nxp; xp += gridDim.x) {
     const T* fx = f + xp * kvol;
     double s0 = 0.0, s2 = 0.0;
-    for (int e = tid; e < kvol; e += kMomThreads) {
+    for (int e = threadIdx.x; e < kvol; e += kMomThreads) {
       const double v = (double)fx[e];
       const int k3 = e % nk - nk / 2, k2 = (e / nk) % nk - nk / 2, k1 = e / (nk * nk) - nk / 2;
       s0 += v;
       s2 += v * (double)(k1 * k1 + k2 * k2 + k3 * k3);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = s0;
-      red[1][tid >> 5] = s2;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < kMomThreads / 32; ++w) {
-        a += red[0][w];
-        b += red[1][w];
-      }
-      bm += a;                 // sum f
-      bk += b;                 // sum |j - N/2|^2 f  (kinetic, in units of dk^2)
-      bv += vx[xp] * a;        // sum V(x) f
-    }
-    __syncthreads();
+    acc[0] += s0;
+    acc[1] += s2;
+    acc[2] += vx[xp] * s0;
   }
-  if (tid == 0) {
-    partials[(int64_t)3 * blockIdx.x + 0] = bm;
-    partials[(int64_t)3 * blockIdx.x + 1] = bk;
-    partials[(int64_t)3 * blockIdx.x + 2] = bv;
-  }
+  block_sum_store<3>(acc, partials);
 }
 
 // Single precision: the FP64 pipe (1/64 of the FP32 rate on this part) cannot keep up with one
-// FP64 add per element at HBM speed, so each thread sums runs of 32 elements in compensated FP32
-// pairs (Knuth's error-free two-sum; the products v |k|^2 with their exact FMA residual) and
-// adds each run's (hi, lo) to FP64 accumulators: about 2^-44 relative per run, the same fixed
-// order on every call (bitwise reproducible), float4 loads.
-
+// FP64 add per element at HBM speed, so each thread sums its elements of an x point in compensated
+// FP32 pairs (Knuth's error-free two-sum; the products v |k|^2 with their exact FMA residual; about
+// 2^-44 relative) and adds the pairs to FP64 accumulators once per x point; float4 loads, eight in
+// flight per thread.
 template <>
 __global__ void __launch_bounds__(kMomThreads) k_moments<float>(const float* __restrict__ f, int64_t nxp,
                                                                 int nk, const double* __restrict__ vx,
                                                                 double* __restrict__ partials) {
-  __shared__ double red[2][kMomThreads / 32];
   const int tid = threadIdx.x;
   const int lg = __ffs(nk) - 1;              // nk is a power of two
   const int kvol4 = (nk * nk * nk) >> 2;     // float4 per x point
   const int half = nk >> 1;
-  constexpr int kRun = 8;                    // float4 loads per compensated run (32 elements)
-  double bm = 0.0, bk = 0.0, bv = 0.0;       // block accumulators (thread 0)
+  double acc[3] = {0.0, 0.0, 0.0};
   for (int64_t xp = blockIdx.x; xp < nxp; xp += gridDim.x) {
     const float4* fx = reinterpret_cast<const float4*>(f + xp * (int64_t)(kvol4 << 2));
-    double s0 = 0.0, s2 = 0.0;
-    int e4 = tid;
-    while (e4 < kvol4) {
-      float h0 = 0.f, l0 = 0.f, h2 = 0.f, l2 = 0.f;
+    float h0 = 0.f, l0 = 0.f, h2 = 0.f, l2 = 0.f;
+#pragma unroll 8
+    for (int e4 = tid; e4 < kvol4; e4 += kMomThreads) {
+      const float4 q = __ldcs(fx + e4);
+      const float v[4] = {q.x, q.y, q.z, q.w};
+      const int e = e4 << 2;
+      const int k1 = (e >> (2 * lg)) - half, k2 = ((e >> lg) & (nk - 1)) - half;
+      const int k3b = (e & (nk - 1)) - half;
 #pragma unroll
-      for (int r = 0; r < kRun; ++r) {
-        if (e4 < kvol4) {
-          const float4 q = __ldcs(fx + e4);
-          const float v[4] = {q.x, q.y, q.z, q.w};
-          const int e = e4 << 2;
-          const int k1 = (e >> (2 * lg)) - half, k2 = ((e >> lg) & (nk - 1)) - half;
-          const int k3b = (e & (nk - 1)) - half;
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int k3 = k3b + c;
-            const float w = (float)(k1 * k1 + k2 * k2 + k3 * k3);   // exact: at most 3 (nk/2)^2
-            two_sum_f(h0, l0, v[c]);
-            const float pr = v[c] * w;
-            l2 += fmaf(v[c], w, -pr);                                 // exact product residual
-            two_sum_f(h2, l2, pr);
-          }
-        }
-        e4 += kMomThreads;
+      for (int c = 0; c < 4; ++c) {
+        const int k3 = k3b + c;
+        const float w = (float)(k1 * k1 + k2 * k2 + k3 * k3);   // exact: at most 3 (nk/2)^2
+        two_sum_f(h0, l0, v[c]);
+        const float pr = v[c] * w;
+        l2 += fmaf(v[c], w, -pr);                                 // exact product residual
+        two_sum_f(h2, l2, pr);
       }
-      s0 += (double)h0 + (double)l0;
-      s2 += (double)h2 + (double)l2;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = s0;
-      red[1][tid >> 5] = s2;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < kMomThreads / 32; ++w) {
-        a += red[0][w];
-        b += red[1][w];
-      }
-      bm += a;
-      bk += b;
-      bv += vx[xp] * a;
-    }
-    __syncthreads();
+    const double s0 = (double)h0 + (double)l0;
+    acc[0] += s0;
+    acc[1] += (double)h2 + (double)l2;
+    acc[2] += vx[xp] * s0;
   }
-  if (tid == 0) {
-    partials[(int64_t)3 * blockIdx.x + 0] = bm;
-    partials[(int64_t)3 * blockIdx.x + 1] = bk;
-    partials[(int64_t)3 * blockIdx.x + 2] = bv;
-  }
+  block_sum_store<3>(acc, partials);
 }
 
 __global__ void k_moments_final(const double* __restrict__ partials, int nblocks, double cell,
