@@ -874,6 +874,63 @@ def run_kernels(args):
                       "peak_gbs": peak}))
 
 
+def run_study_harmonic(args):
+    """The 2-D phase-space harmonic oscillator of Sec. 5.1 through the 6-D solver: f = g(x1, k1)
+    on the slice x2 = x3 = 0, k2 = k3 = 0 of 5-point x2, x3 grids, zero elsewhere (for a quadratic
+    potential the step maps the product factor by factor and these unit factors are fixed points:
+    no displacement along x_d at k_d = 0, no shift along k_d at x_d = 0), so the slice carries the
+    (x1, k1) plane solution: V = kappa/2 x^2,
+    kappa = (pi/5)^2 (period 10), f0 = pi^-1 exp(-(x1 - 1)^2/2 - 2 k1^2), x1 in [-12, 12] in 4
+    PMBC patches, N_k = 32 on [-3.2, 3.2), FP64, Strang with dt = --study-dt over one period.
+    After one period the exact solution is f0 again: eps_inf, eps_2 and eps_mass (Sec. 5) of the
+    plane against f0, for a dx sweep at n_nb = 20 and an n_nb sweep at dx = 0.1."""
+    import numpy as np
+    import torch
+    import paper_2205_02380_gb300 as ch
+    kappa, T, lk, nk = (math.pi / 5) ** 2, 10.0, 3.2, 32
+    dt = args.study_dt
+    nsteps = int(round(T / dt))
+    rows = []
+    stream = torch.cuda.Stream()
+    for nx, n_nb in ((81, 20), (121, 20), (241, 20), (241, 15), (241, 10)):
+        h = 24.0 / (nx - 1)
+        xs = -12.0 + h * np.arange(nx)
+        ks = (np.arange(nk) - nk / 2) * (2 * lk / nk)
+        X, K = np.meshgrid(xs, ks, indexing="ij")
+        g0 = np.exp(-0.5 * (X - 1.0) ** 2 - 2.0 * K ** 2) / math.pi
+        with torch.cuda.stream(stream):
+            s = ch.Solver((nx, 5, 5), nk, (-12.0, -2.0, -2.0), (12.0, 2.0, 2.0), lk, nuclei=[],
+                          kappa=kappa, precision=ch.FP64, n_nb=n_nb, patches=(4, 1, 1),
+                          stream=stream.cuda_stream)
+            f = torch.zeros((nx, 5, 5, nk, nk, nk), device="cuda", dtype=torch.float64)
+            f[:, 2, 2, :, nk // 2, nk // 2] = torch.from_numpy(g0).to("cuda")
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(f, dt, nsteps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            g = f[:, 2, 2, :, nk // 2, nk // 2].cpu().numpy()
+            f[:, 2, 2, :, nk // 2, nk // 2] = 0
+            spread = float(f.abs().max())
+            s.close()
+            del f
+            torch.cuda.empty_cache()
+        d = g - g0
+        cell = h * (2 * lk / nk)
+        rows.append({"nx": nx, "dx": h, "n_nb": n_nb, "eps_inf": float(np.abs(d).max()),
+                     "eps_2": float(np.sqrt((d * d).sum() * cell)),
+                     "eps_mass": float(abs(d.sum()) * cell), "off_slice_max": spread,
+                     "ms_per_step": e0.elapsed_time(e1) / nsteps})
+    dxs = [r for r in rows if r["n_nb"] == 20]
+    order = [math.log(a["eps_inf"] / b["eps_inf"]) / math.log(a["dx"] / b["dx"])
+             for a, b in zip(dxs, dxs[1:])]
+    print(json.dumps({"study": "harmonic oscillator, Sec. 5.1 (2-D phase space, 4 patches)",
+                      "dt": dt, "steps": nsteps, "T": T, "rows": rows,
+                      "order_eps_inf_dx": order}), flush=True)
+
+
 def run_profile(args):
     """FP32 form only on --workload (default the headline one, --nx overrides N_x): init, W
     warm-up steps and K steps, nothing else (for ncu)."""
@@ -913,6 +970,9 @@ def main():
     ap.add_argument("--kernels", action="store_true",
                     help="bandwidth of the reduction, diagnostic and quadratic-potential kernels")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--study", default="", choices=["", "harmonic"],
+                    help="harmonic: the Sec. 5.1 oscillator study (dx and n_nb sweeps)")
+    ap.add_argument("--study-dt", type=float, default=0.005)
     ap.add_argument("--rate", type=float, default=5.0)
     ap.add_argument("--fp64-rate", type=float, default=0.2)
     ap.add_argument("--slots", type=int, default=8)
@@ -933,6 +993,9 @@ def main():
         return
     if args.serve:
         run_serve_mode(args)
+        return
+    if args.study == "harmonic":
+        run_study_harmonic(args)
         return
     if args.oracle_sample:
         print(json.dumps(cpu_baseline_run(args.workload)))

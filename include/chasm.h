@@ -81,7 +81,10 @@ enum { CHASM_THETA_AUTO = 0, CHASM_THETA_TABLE = 1, CHASM_THETA_MODULATED = 2 };
  *     EUNSTABLE when dt rho > 1, rho the spectral-radius bound of Theta_V (chasm_step below). */
 enum { CHASM_STRANG = 0, CHASM_LPC1 = 1 };
 
-/* Grid: points per dimension.  nx[d] >= 4; nk[0] = nk[1] = nk[2] in {8, 16, 32}. */
+/* Grid: points per dimension.  nx[d] >= 4; nk[0] = nk[1] = nk[2] in {8, 16, 32}.  Lines that are
+ * neither 16, 24, 32, 48 nor 64 points long (or patches > 1) are advected in shared memory, which
+ * bounds nx[d]: at most 798 points in FP64 and 1598 in FP32-mixed with one patch (about half that
+ * with patches); chasm_create returns EINVAL beyond. */
 typedef struct {
   int32_t nx[3];
   int32_t nk[3];

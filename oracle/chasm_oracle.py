@@ -528,7 +528,7 @@ def pflow_harmonic(f: np.ndarray, prob: Problem, dt: float) -> np.ndarray:
     return np.real(np.fft.ifftn(F, axes=(3, 4, 5)))
 
 
-def strang_step_plane(g: np.ndarray, prob: Problem, d: int, dt: float) -> np.ndarray:
+def strang_step_plane(g: np.ndarray, prob: Problem, d: int, dt: float, p: int = 1) -> np.ndarray:
     """One Strang step of the quadratic-potential scheme on the (x_d, k_d) plane, g[i, j] at
     (x_{d,i}, k_j).
 
@@ -536,9 +536,12 @@ def strang_step_plane(g: np.ndarray, prob: Problem, d: int, dt: float) -> np.nda
     product over d of 1-D spline interpolations along x_d with shifts set by k_d (Eqs. 3.9, 3.10)
     and P(dt) the product over d of shifts along k_d by dt kappa (x_d - c_d)/hbar (Eq. 5.1).  A
     product f = prod_d g_d(x_d, k_d) is therefore mapped factor by factor, and this function is
-    the factor map (it calls the same 1-D spline and k-shift as the 6-D step)."""
+    the factor map (it calls the same 1-D spline and k-shift as the 6-D step).  p > 1: the x_d
+    axis is split into p PMBC patches (Sec. 3.1.2-3.1.3), as advect_patches does in 6-D."""
     def a_half(gg):
         alpha = prob.hbar * prob.ks() * (0.5 * dt) / (prob.m * prob.hs(d))
+        if p > 1:
+            return advect_1d_patches(gg, 0, prob.hs(d), prob.n_nb, alpha, 1, p)
         return advect_1d(gg, 0, prob.hs(d), prob.n_nb, alpha, 1)
     g = a_half(g)
     g = np.real(np.fft.ifft(np.fft.fft(g, axis=1) * _kshift_factors(prob, d, dt), axis=1))

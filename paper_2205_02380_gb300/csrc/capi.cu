@@ -753,7 +753,7 @@ int chasm_create(const chasm_grid* grid, const chasm_box* box, const chasm_poten
     H->own_stream = true;
   }
   for (int d = 0; d < 3; ++d)
-    if (advect_smem_elems(g.nx[d], o.patches[d]) * kAdvectThreads * H->elt > (size_t)kAdvectMaxSmem) {
+    if (advect_smem_threads(advect_smem_elems(g.nx[d], o.patches[d]), H->elt) == 0) {
       std::string m = "nx[d] too large for the advection kernel's shared-memory line buffer";
       if (H->own_stream) cudaStreamDestroy(H->stream);
       delete H;

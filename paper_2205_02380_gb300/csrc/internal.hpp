@@ -49,6 +49,14 @@ constexpr int kAdvectMaxSmem = 200 * 1024;
 inline size_t advect_smem_elems(int n, int p) {
   return p > 1 ? (size_t)n + 2 * (p + 1) + (size_t)p * ((n - 1) / p + 3) : (size_t)n + 2;
 }
+// threads per block of the shared-memory advection kernels: kAdvectThreads, or fewer (a multiple
+// of 32) for long lines so that the block's line buffers fit kAdvectMaxSmem; 0 if even 32 lines
+// do not fit
+inline int advect_smem_threads(size_t elems, size_t elt) {
+  const size_t per = elems * elt;
+  const int b = (int)std::min<size_t>(kAdvectThreads, (size_t)kAdvectMaxSmem / per / 32 * 32);
+  return b >= 32 ? b : 0;
+}
 cudaError_t advect_prepare();
 cudaError_t launch_advect_dim(const Handle& H, void* f, int dim, cudaStream_t s);
 // Coulomb operator (k_theta.cu): out = (base or 0) + sum_a coef[a] * Theta_a[in]

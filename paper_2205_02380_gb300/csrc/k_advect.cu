@@ -422,7 +422,6 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
   p.w = wbase + (size_t)dim * g.nk * 4;
   p.ns = reinterpret_cast<const int*>(wbase + (size_t)3 * g.nk * 4) + dim * g.nk;
   const int B = kAdvectThreads;
-  const unsigned blocks = (unsigned)((p.n_lines + B - 1) / B);
   const int P = H.opt.patches[dim];
   if (P > 1) {
     PatchArgs<T> q;
@@ -432,8 +431,10 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
     q.W = 2 * q.nb + 1;
     q.win = static_cast<const T*>(H.d_pclos[dim]);
     q.lu = static_cast<const T*>(H.d_plu[dim]);
-    const size_t smem = advect_smem_elems(p.n, P) * B * sizeof(T);
-    k_advect_patches<T><<<blocks, B, smem, s>>>(p, q);
+    const size_t elems = advect_smem_elems(p.n, P);
+    const int Bp = advect_smem_threads(elems, sizeof(T));
+    if (Bp == 0) return cudaErrorInvalidValue;
+    k_advect_patches<T><<<(unsigned)((p.n_lines + Bp - 1) / Bp), Bp, elems * Bp * sizeof(T), s>>>(p, q);
     return cudaGetLastError();
   }
   const bool reg_shift = H.adv.ns_min[dim] >= -2 && H.adv.ns_max[dim] <= 1;
@@ -476,16 +477,18 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
     }
 #undef CHASM_REG
   }
-  const size_t smem = (size_t)(g.nx[dim] + 2) * B * sizeof(T);
-  k_advect_smem<T><<<blocks, B, smem, s>>>(p);
+  const size_t elems = advect_smem_elems(g.nx[dim], 1);
+  const int Bs = advect_smem_threads(elems, sizeof(T));
+  if (Bs == 0) return cudaErrorInvalidValue;
+  k_advect_smem<T><<<(unsigned)((p.n_lines + Bs - 1) / Bs), Bs, elems * Bs * sizeof(T), s>>>(p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t advect_prepare() {
-  // up to (nx + 2) * 128 * sizeof(T) bytes of dynamic shared memory; longer lines are rejected
-  // at create time
+  // up to kAdvectMaxSmem bytes of dynamic shared memory (fewer threads per block for long lines;
+  // lines too long even for 32 threads are rejected at create time)
   cudaError_t e = cudaFuncSetAttribute(k_advect_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kAdvectMaxSmem);
   if (e != cudaSuccess) return e;

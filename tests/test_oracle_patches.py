@@ -59,3 +59,23 @@ def test_3d_patch_advection_with_one_patch_equals_the_64_term_sum():
     a = O.advect(f, prob, 0.3)
     b = O.advect_patches(f, prob, 0.3, (1, 1, 1))
     assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+
+
+def test_plane_step_with_patches():
+    """The plane step with p PMBC patches (Sec. 3.1.2-3.1.3): with full stencils (n_nb >= N) it
+    equals the one-patch plane step (each patch spline is the global spline); with truncated
+    stencils it departs from it (so the patches are applied), by less at n_nb = 15 than at
+    n_nb = 10."""
+    base = dict(nx=(33, 4, 4), nk=8, x_lo=(-8.0, -1.0, -1.0), x_hi=(8.0, 1.0, 1.0), lk=3.0,
+                nuclei=[], kappa=0.4)
+    full = O.Problem(n_nb=40, **base)
+    xs, ks = full.xs(0), full.ks()
+    g = np.exp(-0.5 * (xs[:, None] - 1.0) ** 2 - 2.0 * ks[None, :] ** 2) / np.pi
+    one = O.strang_step_plane(g, full, 0, 0.2)
+    four = O.strang_step_plane(g, full, 0, 0.2, p=4)
+    assert np.max(np.abs(four - one)) <= 1e-13 * np.max(np.abs(one))
+    dev = {}
+    for nb in (10, 15):
+        P = O.Problem(n_nb=nb, **base)
+        dev[nb] = np.max(np.abs(O.strang_step_plane(g, P, 0, 0.2, p=4) - O.strang_step_plane(g, P, 0, 0.2)))
+    assert 0 < dev[15] < dev[10]
