@@ -931,6 +931,53 @@ def run_study_harmonic(args):
                       "order_eps_inf_dx": order}), flush=True)
 
 
+def run_study_tkm(args):
+    """Example 4.1 on the GPU: Phi = |k|^-2 * exp(-|k|^2) by chasm_tkm_convolve (the TKM of Sec. 4)
+    for N_k = 8, 16, 32 on [-4, 4)^3, against the closed form 2 pi^{3/2} F(k)/k (F = Dawson's
+    integral, scipy.special.dawsn): eps_inf = max |Phi - Phi_exact|, eps_2 = (sum (Phi -
+    Phi_exact)^2 dk^3)^{1/2}, and the time per Phi (one x point) when 32^3 of them are computed in
+    one call (CUDA events, mean of 5 calls), in both forms."""
+    import numpy as np
+    import torch
+    from scipy.special import dawsn
+    import paper_2205_02380_gb300 as ch
+    lk, nx = 4.0, 32
+    rows = []
+    stream = torch.cuda.Stream()
+    for prec, dtp, name in ((ch.FP64, torch.float64, "fp64"), (ch.FP32_MIXED, torch.float32, "fp32")):
+        for nk in (8, 16, 32):
+            dk = 2 * lk / nk
+            ks = (np.arange(nk) - nk / 2) * dk
+            K = np.sqrt(ks[:, None, None] ** 2 + ks[None, :, None] ** 2 + ks[None, None, :] ** 2)
+            Kp = np.where(K > 0, K, 1.0)
+            ex = np.where(K > 0, 2 * math.pi ** 1.5 * dawsn(Kp) / Kp, 2 * math.pi ** 1.5)
+            with torch.cuda.stream(stream):
+                s = ch.Solver(nx, nk, -12.0, 12.0, lk, nuclei=[((0.0, 0.0, 0.0), 1.0)],
+                              theta_form=ch.THETA_TABLE, precision=prec, stream=stream.cuda_stream)
+                g = torch.from_numpy(np.exp(-K ** 2)).to("cuda", dtp).expand(
+                    (nx,) * 3 + (nk,) * 3).contiguous()
+                out = torch.empty_like(g)
+                s.tkm_convolve(g, out)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(5):
+                    s.tkm_convolve(g, out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 5
+                phi = out[0, 0, 0].double().cpu().numpy()
+                s.close()
+                del g, out
+                torch.cuda.empty_cache()
+            d = phi - ex
+            rows.append({"form": name, "nk": nk, "eps_inf": float(np.abs(d).max()),
+                         "eps_2": float(np.sqrt((d * d).sum() * dk ** 3)),
+                         "s_per_phi": ms / 1e3 / nx ** 3, "ms_per_call": ms, "points": nx ** 3})
+    print(json.dumps({"study": "Example 4.1 (TKM, Gaussian), L_k = 4", "rows": rows}), flush=True)
+
+
 def run_profile(args):
     """FP32 form only on --workload (default the headline one, --nx overrides N_x): init, W
     warm-up steps and K steps, nothing else (for ncu)."""
@@ -970,8 +1017,9 @@ def main():
     ap.add_argument("--kernels", action="store_true",
                     help="bandwidth of the reduction, diagnostic and quadratic-potential kernels")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
-    ap.add_argument("--study", default="", choices=["", "harmonic"],
-                    help="harmonic: the Sec. 5.1 oscillator study (dx and n_nb sweeps)")
+    ap.add_argument("--study", default="", choices=["", "harmonic", "tkm"],
+                    help="harmonic: the Sec. 5.1 oscillator study (dx and n_nb sweeps); "
+                         "tkm: the Example 4.1 table")
     ap.add_argument("--study-dt", type=float, default=0.005)
     ap.add_argument("--rate", type=float, default=5.0)
     ap.add_argument("--fp64-rate", type=float, default=0.2)
@@ -996,6 +1044,9 @@ def main():
         return
     if args.study == "harmonic":
         run_study_harmonic(args)
+        return
+    if args.study == "tkm":
+        run_study_tkm(args)
         return
     if args.oracle_sample:
         print(json.dumps(cpu_baseline_run(args.workload)))

@@ -191,6 +191,14 @@ int chasm_pflow(chasm_handle* h, void* f_dev, double dt);
  * kappa = 0 without nuclei. */
 int chasm_theta(chasm_handle* h, const void* u_dev, void* out_dev);
 
+/* phi = T * g: the truncated-kernel convolution of Sec. 4 without the modulation of Eq. 4.6,
+ * phi(x, k_p) = sum_q T_{p-q} g(x, k_q) for every x point, with T of Eq. 4.7 (T carries dk^3, so
+ * phi approximates the convolution (1/|k|^2 * g)(k) of Example 4.1).  g and phi have the layout
+ * and element type of f; they must not alias.  Coulomb handles in the table form only (EINVAL
+ * otherwise); the first call builds the spectrum of T on the handle's stream (one x point's worth
+ * of the per-x table, FP64 precompute) and keeps it until chasm_destroy.  Asynchronous. */
+int chasm_tkm_convolve(chasm_handle* h, const void* g_dev, void* phi_dev);
+
 /* Mass h1 h2 h3 dk^3 sum f and energy h1 h2 h3 dk^3 sum (hbar^2 |k|^2 / 2m + V(x)) f, both
  * accumulated in FP64 with a fixed reduction tree (bitwise reproducible); synchronous. */
 int chasm_mass(chasm_handle* h, const void* f_dev, double* out);

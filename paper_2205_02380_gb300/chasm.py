@@ -89,6 +89,7 @@ _SIGS = [
     ("chasm_advect", C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
     ("chasm_pflow", C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
     ("chasm_theta", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("chasm_tkm_convolve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("chasm_mass", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("chasm_energy", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("chasm_moments", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -283,6 +284,10 @@ class Solver:
     def theta(self, u, out):
         """chasm_theta: out = Theta^T[u] (the Coulomb operator, or kappa (x - c)/hbar . grad_k u)."""
         self._call(lib().chasm_theta, _ptr(u), _ptr(out))
+
+    def tkm_convolve(self, g, phi):
+        """chasm_tkm_convolve: phi = T * g per x point (the TKM convolution of Sec. 4)."""
+        self._call(lib().chasm_tkm_convolve, _ptr(g), _ptr(phi))
 
     def moments(self, f):
         """chasm_moments: (mass, energy) of f, FP64, bitwise reproducible."""

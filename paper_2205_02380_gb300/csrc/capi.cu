@@ -497,7 +497,7 @@ void free_all(Handle* H) {
   void* ptrs[] = {H->d_clos[0], H->d_clos[1], H->d_clos[2], H->d_lu[0], H->d_lu[1], H->d_lu[2],
                   H->d_pclos[0], H->d_pclos[1], H->d_pclos[2], H->d_plu[0], H->d_plu[1], H->d_plu[2],
                   H->adv.dev, H->d_T,
-                  H->d_that, H->d_phase, H->d_sig, H->d_scratch, H->d_u[0], H->d_u[1], H->d_krows,
+                  H->d_that, H->d_phase, H->d_sig, H->d_tkm, H->d_scratch, H->d_u[0], H->d_u[1], H->d_krows,
                   H->d_partials, H->d_result, H->d_vx, H->d_diag, H->d_fhost};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, H->stream);
@@ -926,6 +926,33 @@ int chasm_theta(chasm_handle* h, const void* u, void* out) {
   if (((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(out)) & 15) != 0)
     return fail(H, CHASM_EINVAL, "u/out must be 16-byte aligned");
   return theta_any(H, u, nullptr, out, 1.0);
+}
+
+int chasm_tkm_convolve(chasm_handle* h, const void* g, void* phi) {
+  Handle* H = reinterpret_cast<Handle*>(h);
+  if (!H) return fail(nullptr, CHASM_EINVAL, "handle is NULL");
+  if (H->nuclei.empty()) return fail(H, CHASM_EINVAL, "chasm_tkm_convolve needs a Coulomb handle");
+  if (!H->xs) return fail(H, CHASM_EINVAL, "chasm_tkm_convolve needs the table form of Theta (theta_form)");
+  if (!g || !phi) return fail(H, CHASM_EINVAL, "g/phi is NULL");
+  if (g == phi) return fail(H, CHASM_EINVAL, "g and phi must not alias");
+  if (((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(phi)) & 15) != 0)
+    return fail(H, CHASM_EINVAL, "g/phi must be 16-byte aligned");
+  if (!H->d_tkm) {   // the spectrum of T, built once per handle on first use
+    const int N = H->g.nk;
+    const size_t bytes = (size_t)4 * N * N * N * H->elt;
+    if (cudaMallocAsync(&H->d_tkm, bytes, H->stream) != cudaSuccess) {
+      H->d_tkm = nullptr;
+      return fail(H, CHASM_ENOMEM, "chasm_tkm_convolve: table allocation failed");
+    }
+    const cudaError_t e = build_tkm_table(*H, H->d_tkm, H->stream);
+    if (e != cudaSuccess) return cuda_fail(H, e, "build_tkm_table");
+  }
+  XsExtra x;
+  x.sig = H->d_tkm;
+  x.real_symbol = true;
+  const double one = 1.0;
+  CHASM_CUDA(H, launch_theta_xs(*H, g, nullptr, phi, 1, &one, H->stream, x));
+  return CHASM_OK;
 }
 
 int chasm_moments(chasm_handle* h, const void* f, double* mass, double* energy) {

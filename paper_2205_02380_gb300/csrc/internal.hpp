@@ -75,6 +75,10 @@ struct XsExtra {
   const void* in2 = nullptr;
   const void* base2 = nullptr;
   double cin2 = 0.0, cbase2 = 0.0;
+  // the plain TKM convolution (chasm_tkm_convolve): sig replaces the per-x table, one table for
+  // every x point, holding the real spectrum of T (the output is then T * in, no sine kernel)
+  const void* sig = nullptr;
+  bool real_symbol = false;
 };
 cudaError_t launch_theta_xs(const Handle& H, const void* in, const void* base, void* out, int nst,
                             const double* coef, cudaStream_t s, const XsExtra& x = XsExtra());
@@ -96,6 +100,9 @@ cudaError_t measure_fma_peak_f32x2(double* tflops);
 // the per-x symbol table (k_xsym.cu), [nxp][N][2N][2N] in the storage type; needs H.d_T
 size_t xs_table_bytes(int nk, int64_t nxp, size_t elt);
 cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s);
+// the spectrum of T on the same frequencies, (2 / (2N)^3) sum_m T_m e^{-i omega . m} (real: T is
+// even), one x point's worth of table in the layout of the per-x table; needs H.d_T
+cudaError_t build_tkm_table(const Handle& H, void* out, cudaStream_t s);
 // Packed single-precision variant of the table-form P(dt) kernel (k_theta_pk.cu), used for
 // FP32-mixed handles with N_k = 16 or 32: its symbol table has the layout
 // [x][j][xi1 / 4][xi2][xi1 % 4] (k_xsym.cu writes it), the other cases [x][j][s1][s2]
@@ -169,6 +176,7 @@ struct Handle {
   void* d_phase = nullptr;         // modulation tables (storage type complex)
   bool xs = false;                 // table (real) form of Theta^T, else the modulated form
   void* d_sig = nullptr;           // per-x symbol table of the table form
+  void* d_tkm = nullptr;           // spectrum of T in the table layout (chasm_tkm_convolve)
   ThetaPlan theta;                 // launch plan of the Theta kernel
   void* d_scratch = nullptr;       // per-CTA scratch of the global-scratch Theta kernel
   void* d_u[2] = {nullptr, nullptr};  // Horner buffers

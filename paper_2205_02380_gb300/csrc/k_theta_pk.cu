@@ -47,8 +47,9 @@ struct PkParams {
   float* out;          // result of the last stage; may alias in, in2, base and base2
   int64_t nxp;
   const float* sig;    // [nxp][N][L/4][L][4] symbol table
+  int64_t sig_xs;      // floats per x point of sig (0: one table for every x point)
   int nst;             // stages, 1..4
-  float ncoef[4];      // -c_s per stage (the sign of the deferred factor i)
+  float ncoef[4];      // -c_s per stage (the sign of the deferred factor i); +c_s when REAL
   float4* G;           // per-CTA spectrum scratch [N][N/2][N] when it is not in shared memory
 };
 
@@ -239,8 +240,10 @@ __device__ __forceinline__ void slab_rows_inverse(float4* g, const float* vrow, 
   });
 }
 
-// X2: the second input and base terms (in2, base2) are read (the LPC1 corrector)
-template <int N, bool X2>
+// X2: the second input and base terms (in2, base2) are read (the LPC1 corrector).  REAL: the
+// table holds the real spectrum of an even kernel (the plain TKM convolution with T): no deferred
+// factor i, the result is Re[e^{i phi} y].
+template <int N, bool X2, bool REAL = false>
 __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const PkParams p) {
   using C = PkCfg<N>;
   constexpr int NT = C::NT, NW = C::NW, SPW = C::SPW, L = C::L, RS = C::RS;
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
           const int sn = s0 + NW * SPW < N ? s0 + NW * SPW : warp * SPW;
           const int64_t xn = s0 + NW * SPW < N || st + 1 < p.nst ? xp : xp + gridDim.x;
           if (xn < p.nxp)
-            bulk_prefetch_l2(p.sig + (xn * N + sn) * (int64_t)(L * L), SPW * L * L * sizeof(float));
+            bulk_prefetch_l2(p.sig + xn * p.sig_xs + sn * (int64_t)(L * L), SPW * L * L * sizeof(float));
         }
         float* Vs = Vw + sub * N * RS;
         float4* gs = G + (size_t)(s0 + sub) * SQ;
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
 #pragma unroll 1
         for (int rnd = 0; rnd < 2; ++rnd) {
           const int cc = lane + 32 * rnd, sc = cc / L, c = cc % L;
-          const float4* sg = reinterpret_cast<const float4*>(p.sig) + (xp * N + s0 + sc) * (int64_t)(L * L / 4);
+          const float4* sg = reinterpret_cast<const float4*>(p.sig + xp * p.sig_xs) + (s0 + sc) * (int64_t)(L * L / 4);
           slab_column<N>(Vw + sc * N * RS, c, sg, spol);
         }
         __syncwarp();
@@ -339,7 +342,8 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
         sfor<0, N>([&](auto I) {   // v = base - c_s (sin phi Re y + cos phi Im y), phi = pi n/(2N)
           constexpr int n = decltype(I)::value;
           constexpr float c = CS<n, 4 * N>::c, s = CS<n, 4 * N>::s;
-          const float2 th = fma2(y[n].im, f2(c, c), mul2(y[n].re, f2(s, s)));
+          const float2 th = REAL ? fma2(y[n].re, f2(c, c), mul2(y[n].im, f2(-s, -s)))   // Re[e^{i phi} y]
+                                 : fma2(y[n].im, f2(c, c), mul2(y[n].re, f2(s, s)));
           a[n] = fmaf(nc, th.x, a[n]);
           b[n] = fmaf(nc, th.y, b[n]);
         });
@@ -361,6 +365,8 @@ void plan_pk_n(int64_t nxp, int num_sms, ThetaPlan* pl) {
   using C = PkCfg<N>;
   int nb = 0;
   cudaFuncSetAttribute(k_theta_pk<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes);
+  cudaFuncSetAttribute(k_theta_pk<N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)C::smem_bytes);
   if (cudaFuncSetAttribute(k_theta_pk<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)C::smem_bytes) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_theta_pk<N, false>, C::NT, C::smem_bytes) !=
@@ -385,14 +391,19 @@ cudaError_t launch_pk_n(const Handle& H, const void* in, const void* base, void*
   p.cbase2 = (float)x.cbase2;
   p.out = static_cast<float*>(out);
   p.nxp = H.g.nxp;
-  p.sig = static_cast<const float*>(H.d_sig);
+  p.sig = static_cast<const float*>(x.sig ? x.sig : H.d_sig);
+  p.sig_xs = x.sig ? 0 : (int64_t)N * C::L * C::L;
   p.nst = nst;
-  for (int q = 0; q < 4; ++q) p.ncoef[q] = q < nst ? (float)(-coef[q]) : 0.f;
+  for (int q = 0; q < 4; ++q) p.ncoef[q] = q < nst ? (float)(x.real_symbol ? coef[q] : -coef[q]) : 0.f;
   p.G = static_cast<float4*>(H.d_scratch);
-  if (x.in2 || x.base2)
+  if (x.real_symbol) {
+    if (x.in2 || x.base2) return cudaErrorInvalidValue;
+    k_theta_pk<N, false, true><<<H.theta.blocks, C::NT, C::smem_bytes, s>>>(p);
+  } else if (x.in2 || x.base2) {
     k_theta_pk<N, true><<<H.theta.blocks, C::NT, C::smem_bytes, s>>>(p);
-  else
+  } else {
     k_theta_pk<N, false><<<H.theta.blocks, C::NT, C::smem_bytes, s>>>(p);
+  }
   return cudaGetLastError();
 }
 

@@ -45,6 +45,7 @@ struct XsParams {
   T* out;          // result of the last stage; may alias in, in2, base and base2
   int64_t nxp;
   const T* sig;    // [nxp][N][2N][2N] symbol table
+  int64_t sig_xs;  // elements per x point of sig (0: one table for every x point)
   int nst;         // stages, 1..4
   T coef[4];       // c_s per stage
   cpx<T>* G;       // per-CTA spectrum scratch (N^3 complex) when it is not in shared memory
@@ -191,8 +192,9 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes
 }
 
 // X2: the second input and base terms (in2, base2) are read (the LPC1 corrector); without it
-// they are compiled out
-template <typename T, int N, int NT, bool GSM, int MINB, bool X2>
+// they are compiled out.  IMAG: the table is the imaginary part sigma of the symbol i sigma (the
+// Coulomb operator); without it the real spectrum of an even kernel (the plain TKM convolution).
+template <typename T, int N, int NT, bool GSM, int MINB, bool X2, bool IMAG = true>
 __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
   using C = XsCfg<T, N>;
   constexpr int L = C::L, GS = C::GS, NG = C::NG, SR = C::SR, SLAB = C::SLAB;
@@ -228,10 +230,10 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
         if (tg == 0) {   // the symbol slab this group needs next, into L2 (one bulk prefetch)
           const int sn = s + NG < N ? s + NG : grp;
           const int64_t xn = s + NG < N || st + 1 < p.nst ? xp : xp + gridDim.x;
-          if (xn < p.nxp) bulk_prefetch_l2(p.sig + (xn * N + sn) * (int64_t)(L * L), L * L * sizeof(T));
+          if (xn < p.nxp) bulk_prefetch_l2(p.sig + xn * p.sig_xs + sn * (int64_t)(L * L), L * L * sizeof(T));
         }
-        slab_conv<T, N, GS, SR, !GSM, true>(G + (size_t)s * SLAB, V,
-                                            p.sig + (xp * N + s) * (int64_t)(L * L), tg, grp, pol);
+        slab_conv<T, N, GS, SR, !GSM, IMAG>(G + (size_t)s * SLAB, V,
+                                            p.sig + xp * p.sig_xs + s * (int64_t)(L * L), tg, grp, pol);
       }
       __syncthreads();
 
@@ -262,10 +264,10 @@ __global__ void __launch_bounds__(NT, MINB) k_theta_xs(const XsParams<T> p) {
   }
 }
 
-template <typename T, int N, bool X2 = false>
+template <typename T, int N, bool X2 = false, bool IMAG = true>
 auto xs_kernel() {
   using C = XsCfg<T, N>;
-  return k_theta_xs<T, N, C::NT, C::GSM, C::MINB, X2>;
+  return k_theta_xs<T, N, C::NT, C::GSM, C::MINB, X2, IMAG>;
 }
 
 template <typename T, int N>
@@ -274,6 +276,8 @@ void plan_xs_tn(int64_t nxp, int num_sms, ThetaPlan* pl) {
   auto kern = xs_kernel<T, N>();
   int nb = 0;
   cudaFuncSetAttribute(xs_kernel<T, N, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)C::smem_bytes);
+  cudaFuncSetAttribute(xs_kernel<T, N, false, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)C::smem_bytes);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes) !=
           cudaSuccess ||
@@ -298,14 +302,19 @@ cudaError_t launch_xs_tn(const Handle& H, const void* in, const void* base, void
   p.cbase2 = (T)x.cbase2;
   p.out = static_cast<T*>(out);
   p.nxp = H.g.nxp;
-  p.sig = static_cast<const T*>(H.d_sig);
+  p.sig = static_cast<const T*>(x.sig ? x.sig : H.d_sig);
+  p.sig_xs = x.sig ? 0 : (int64_t)N * C::L * C::L;
   p.nst = nst;
   for (int q = 0; q < 4; ++q) p.coef[q] = q < nst ? (T)coef[q] : (T)0;
   p.G = static_cast<cpx<T>*>(H.d_scratch);
-  if (x.in2 || x.base2)
+  if (x.real_symbol) {
+    if (x.in2 || x.base2) return cudaErrorInvalidValue;
+    k_theta_xs<T, N, C::NT, C::GSM, C::MINB, false, false><<<H.theta.blocks, C::NT, C::smem_bytes, s>>>(p);
+  } else if (x.in2 || x.base2) {
     k_theta_xs<T, N, C::NT, C::GSM, C::MINB, true><<<H.theta.blocks, C::NT, C::smem_bytes, s>>>(p);
-  else
+  } else {
     k_theta_xs<T, N, C::NT, C::GSM, C::MINB, false><<<H.theta.blocks, C::NT, C::smem_bytes, s>>>(p);
+  }
   return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ struct XsGeom {
   int n_nuc;
   double pos[kMaxNuclei][3];
   double g[kMaxNuclei];
+  int plain;   // 1: the sg = 1 terms are dropped (the spectrum of T itself, build_tkm_table)
 };
 
 // C[A][i][sg][xi][m] = scale w(m) cos(omega(xi) m - s a m), s = +1 (sg = 0) or -1 (sg = 1),
@@ -65,6 +66,7 @@ __global__ void k_xs_costab(double* __restrict__ C, XsGeom G, int d, int nxi) {
   sincos(a * m, &sb, &cb);
   double v = (m == 0 ? 1.0 : 2.0) * (ca * cb + s * sa * sb);
   if (d == 0) v *= s * G.g[A];
+  if (G.plain && sg == 1) v = 0.0;
   C[t] = v;
 }
 
@@ -194,27 +196,9 @@ cudaError_t table_chunk(bool fp64, int N, const double* C1, const double* R2, vo
   return cudaErrorInvalidValue;
 }
 
-}  // namespace
-
-size_t xs_table_bytes(int nk, int64_t nxp, size_t elt) { return (size_t)nxp * 4 * nk * nk * nk * elt; }
-
-cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s) {
-  XsGeom G{};
-  const int N = H.g.nk, L = 2 * N;
-  G.N = N;
-  G.L = L;
-  for (int d = 0; d < 3; ++d) {
-    G.nx[d] = H.g.nx[d];
-    G.x_lo[d] = H.g.x_lo[d];
-    G.h[d] = H.g.h[d];
-  }
-  G.dk = H.g.dk;
-  G.n_nuc = (int)H.nuclei.size();
-  if (G.n_nuc < 1 || G.n_nuc > kMaxNuclei || !H.d_T) return cudaErrorInvalidValue;
-  for (int a = 0; a < G.n_nuc; ++a) {
-    for (int d = 0; d < 3; ++d) G.pos[a][d] = H.nuclei[a].pos[d];
-    G.g[a] = 2.0 * H.nuclei[a].charge / (M_PI * M_PI * H.hbar * (double)L * L * L);
-  }
+// the three cosine tables, R3, then per chunk of x2 planes R2 and the table
+cudaError_t run_table(const XsGeom& G, bool fp64, const double* Tfull, void* sig, cudaStream_t s) {
+  const int N = G.N, L = G.L;
   const int64_t n1 = (int64_t)G.n_nuc * G.nx[0] * 2 * L * N;
   const int64_t n2 = (int64_t)G.n_nuc * G.nx[1] * 2 * L * N;
   const int64_t n3 = (int64_t)G.n_nuc * G.nx[2] * 2 * N * N;
@@ -237,18 +221,63 @@ cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s) {
     k_xs_costab<<<nblk(n1, 256), 256, 0, s>>>(C1, G, 0, L);
     k_xs_costab<<<nblk(n2, 256), 256, 0, s>>>(C2, G, 1, L);
     k_xs_costab<<<nblk(n3, 256), 256, 0, s>>>(C3, G, 2, N);
-    k_xs_r3<<<nblk(nr3, 256), 256, 0, s>>>(C3, H.d_T, R3, G);
+    k_xs_r3<<<nblk(nr3, 256), 256, 0, s>>>(C3, Tfull, R3, G);
     e = cudaGetLastError();
   }
   for (int i2 = 0; e == cudaSuccess && i2 < G.nx[1]; i2 += c2) {
     const int cc = std::min(c2, G.nx[1] - i2);
     k_xs_r2<<<nblk(per_i2 * cc, 256), 256, 0, s>>>(C2, R3, R2, G, i2, cc);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = table_chunk(H.fp64, N, C1, R2, sig, G, i2, cc, s);
+    if (e == cudaSuccess) e = table_chunk(fp64, N, C1, R2, sig, G, i2, cc, s);
   }
   for (double* p : {C1, C2, C3, R3, R2})
     if (p) cudaFreeAsync(p, s);
   return e;
+}
+
+}  // namespace
+
+size_t xs_table_bytes(int nk, int64_t nxp, size_t elt) { return (size_t)nxp * 4 * nk * nk * nk * elt; }
+
+cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s) {
+  XsGeom G{};
+  const int N = H.g.nk, L = 2 * N;
+  G.N = N;
+  G.L = L;
+  for (int d = 0; d < 3; ++d) {
+    G.nx[d] = H.g.nx[d];
+    G.x_lo[d] = H.g.x_lo[d];
+    G.h[d] = H.g.h[d];
+  }
+  G.dk = H.g.dk;
+  G.n_nuc = (int)H.nuclei.size();
+  if (G.n_nuc < 1 || G.n_nuc > kMaxNuclei || !H.d_T) return cudaErrorInvalidValue;
+  for (int a = 0; a < G.n_nuc; ++a) {
+    for (int d = 0; d < 3; ++d) G.pos[a][d] = H.nuclei[a].pos[d];
+    G.g[a] = 2.0 * H.nuclei[a].charge / (M_PI * M_PI * H.hbar * (double)L * L * L);
+  }
+  return run_table(G, H.fp64, H.d_T, sig, s);
+}
+
+// One x point at the (virtual) nucleus (a = 0), only the sg = 0 terms: sum_m T_m prod_d w(m_d)
+// cos(omega_d m_d) = sum over all m in (-N, N)^3 of T_m e^{-i omega . m} (T even in every m_d),
+// times 2 / (2N)^3 as the per-x table carries.
+cudaError_t build_tkm_table(const Handle& H, void* out, cudaStream_t s) {
+  XsGeom G{};
+  const int N = H.g.nk, L = 2 * N;
+  G.N = N;
+  G.L = L;
+  for (int d = 0; d < 3; ++d) {
+    G.nx[d] = 1;
+    G.x_lo[d] = 0.0;
+    G.h[d] = 1.0;
+  }
+  G.dk = H.g.dk;
+  G.n_nuc = 1;
+  G.g[0] = 2.0 / ((double)L * L * L);
+  G.plain = 1;
+  if (!H.d_T) return cudaErrorInvalidValue;
+  return run_table(G, H.fp64, H.d_T, out, s);
 }
 
 }  // namespace chasm
