@@ -978,6 +978,46 @@ def run_study_tkm(args):
     print(json.dumps({"study": "Example 4.1 (TKM, Gaussian), L_k = 4", "rows": rows}), flush=True)
 
 
+def run_long(args):
+    """A full-length run of one workload in both forms from the same initial data (FP64 first; its
+    result stays on the device while the FP32-mixed form runs): the relative L2 distance of the
+    FP32-mixed result from the FP64 one, and per form the relative drift of mass and energy and
+    the step time.  --long electron-proton runs its 100 steps (dt 0.02)."""
+    import torch
+    import paper_2205_02380_gb300 as ch
+    W = WORKLOADS[args.long]
+    steps = args.long_steps
+    stream = torch.cuda.Stream()
+    out, final = {}, None
+    with torch.cuda.stream(stream):
+        for name, prec, dtp in (("fp64", ch.FP64, torch.float64), ("fp32", ch.FP32_MIXED, torch.float32)):
+            s = make_solver(ch, W, prec, stream)
+            f = new_f(torch, W, dtp)
+            init_f(s, W, f)
+            m0, e0 = s.moments(f)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            s.step(f, W["dt"], steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            m1, e1 = s.moments(f)
+            out[name] = {"ms_per_step": ev0.elapsed_time(ev1) / steps, "mass_drift": (m1 - m0) / m0,
+                         "energy0": e0, "energy_drift": (e1 - e0) / abs(e0)}
+            s.close()
+            if name == "fp64":
+                final = f
+            else:
+                num = torch.linalg.vector_norm(f.double() - final)
+                out["rel_l2_fp32_vs_fp64"] = float(num / torch.linalg.vector_norm(final))
+                out["mass_rel_diff_fp32_vs_fp64"] = (out["fp32"]["mass_drift"] - out["fp64"]["mass_drift"])
+            del f
+            torch.cuda.empty_cache()
+    print(json.dumps({"long_run": W["name"], "steps": steps, "t_final": steps * W["dt"],
+                      "tolerance": 1e-5, **out}), flush=True)
+
+
 def run_profile(args):
     """FP32 form only on --workload (default the headline one, --nx overrides N_x): init, W
     warm-up steps and K steps, nothing else (for ncu)."""
@@ -1021,6 +1061,9 @@ def main():
                     help="harmonic: the Sec. 5.1 oscillator study (dx and n_nb sweeps); "
                          "tkm: the Example 4.1 table")
     ap.add_argument("--study-dt", type=float, default=0.005)
+    ap.add_argument("--long", default="", choices=[""] + sorted(WORKLOADS),
+                    help="full-length run of a workload in both forms (see --long-steps)")
+    ap.add_argument("--long-steps", type=int, default=100)
     ap.add_argument("--rate", type=float, default=5.0)
     ap.add_argument("--fp64-rate", type=float, default=0.2)
     ap.add_argument("--slots", type=int, default=8)
@@ -1047,6 +1090,9 @@ def main():
         return
     if args.study == "tkm":
         run_study_tkm(args)
+        return
+    if args.long:
+        run_long(args)
         return
     if args.oracle_sample:
         print(json.dumps(cpu_baseline_run(args.workload)))
