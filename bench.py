@@ -116,7 +116,7 @@ def measured_hbm_gbs():
 def theta_source_hash() -> str:
     """Hash of the sources of the P(dt) kernel (the traffic figure is void once they change)."""
     h = hashlib.sha256()
-    for name in ("k_theta_xs.cu", "fft_reg.cuh"):
+    for name in ("k_theta_pk.cu", "fft_pk.cuh", "fft_reg.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2205_02380_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -663,8 +663,8 @@ def run_chasm(args):
         "stationarity": stat,
         "lpc1": lpc1,
         "serving": serving,
-        "roofline": {"kernel": "k_theta_xs (P(dt): four Horner stages of Theta^T per x point, "
-                               "table form)",
+        "roofline": {"kernel": "k_theta_pk<32> (P(dt): four Horner stages of Theta^T per x point, "
+                               "table form, packed FP32)",
                      "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "peak_source": f"derived: {num_sms} SMs x 128 FP32 lanes x 2 x max SM clock",
