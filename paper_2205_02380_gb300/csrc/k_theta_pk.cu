@@ -132,6 +132,51 @@ __device__ __forceinline__ void store_pair(float* dst, const float (&a)[N], cons
   }
 }
 
+// The line pairs of one warp in a k3 pass (N = 32): lane k1 owns the pair (k1, k2 = 2m, 2m + 1)
+// with m common to the warp, i.e. 2N contiguous floats at src_m + k1 N^2.  Read through the warp's
+// slab buffer so that every global access of the warp covers two whole pairs (512 contiguous
+// bytes) instead of one 16-byte piece of 32 pairs: the loads no longer depend on L1 to merge.
+template <int N>
+__device__ __forceinline__ void warp_load_pairs(const float* src_m, float* T, float (&a)[N], float (&b)[N]) {
+  constexpr int Q = N / 2, RW = 2 * N + 4;   // quads per pair, buffer row (floats)
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int t = 2 * q + (lane >> 4), e = lane & 15;
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(src_m + (size_t)t * N * N) + e);
+    *reinterpret_cast<float4*>(T + t * RW + 4 * e) = v;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float4 v = *reinterpret_cast<const float4*>(T + lane * RW + 4 * q);
+    float* d = q < Q / 2 ? a + 4 * q : b + 4 * (q - Q / 2);
+    d[0] = v.x;
+    d[1] = v.y;
+    d[2] = v.z;
+    d[3] = v.w;
+  }
+  __syncwarp();
+}
+template <int N>
+__device__ __forceinline__ void warp_store_pairs(float* dst_m, float* T, const float (&a)[N], const float (&b)[N]) {
+  constexpr int Q = N / 2, RW = 2 * N + 4;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float* d = q < Q / 2 ? a + 4 * q : b + 4 * (q - Q / 2);
+    *reinterpret_cast<float4*>(T + lane * RW + 4 * q) = make_float4(d[0], d[1], d[2], d[3]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int t = 2 * q + (lane >> 4), e = lane & 15;
+    __stcs(reinterpret_cast<float4*>(dst_m + (size_t)t * N * N) + e,
+           *reinterpret_cast<const float4*>(T + t * RW + 4 * e));
+  }
+  __syncwarp();
+}
+
 // k3 forward of a real line pair: twist by e^{-i pi n/(2N)}, FFT_N, spectrum quads out
 template <int N, bool GSM>
 __device__ __forceinline__ void k3_forward(const float (&a)[N], const float (&b)[N], float4* g,
@@ -261,11 +306,14 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
   auto phase_a = [&](int64_t xq, int pr) {
     const int k1 = pr % N, m = pr / N;
     const size_t off = (size_t)xq * N3 + ((size_t)k1 * N + 2 * m) * N;
+    const size_t offm = (size_t)xq * N3 + (size_t)2 * m * N;   // the warp's common part (N = 32)
     float a[N], b[N];
-    load_pair<N>(p.in + off, a, b);
+    if constexpr (!GSM) warp_load_pairs<N>(p.in + offm, Vw, a, b);
+    else load_pair<N>(p.in + off, a, b);
     if (X2 && p.in2) {   // u_0 = in + cin2 in2 (the LPC1 predictor)
       float a2[N], b2[N];
-      load_pair<N>(p.in2 + off, a2, b2);
+      if constexpr (!GSM) warp_load_pairs<N>(p.in2 + offm, Vw, a2, b2);
+      else load_pair<N>(p.in2 + off, a2, b2);
 #pragma unroll
       for (int n = 0; n < N; ++n) {
         a[n] = fmaf(p.cin2, a2[n], a[n]);
@@ -315,6 +363,7 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
       for (int pr = tid; pr < NP; pr += NT) {
         const int k1 = pr % N, m = pr / N;
         const size_t off = (size_t)xp * N3 + ((size_t)k1 * N + 2 * m) * N;
+        const size_t offm = (size_t)xp * N3 + (size_t)2 * m * N;
         float4* g = G + (size_t)m * N + k1;
         pc y[N];
 #pragma unroll
@@ -325,10 +374,12 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
         fft_pk<N, true>(y);
         float a[N], b[N];   // Horner base of the two lines
         if (p.base) {
-          load_pair<N>(p.base + off, a, b);
+          if constexpr (!GSM) warp_load_pairs<N>(p.base + offm, Vw, a, b);
+          else load_pair<N>(p.base + off, a, b);
           if (X2 && p.base2) {
             float a2[N], b2[N];
-            load_pair<N>(p.base2 + off, a2, b2);
+            if constexpr (!GSM) warp_load_pairs<N>(p.base2 + offm, Vw, a2, b2);
+            else load_pair<N>(p.base2 + off, a2, b2);
 #pragma unroll
             for (int n = 0; n < N; ++n) {
               a[n] = fmaf(p.cbase2, a2[n], a[n]);
@@ -348,7 +399,8 @@ __global__ void __launch_bounds__(PkCfg<N>::NT, PkCfg<N>::MINB) k_theta_pk(const
           b[n] = fmaf(nc, th.y, b[n]);
         });
         if (last) {
-          store_pair<N>(p.out + off, a, b);
+          if constexpr (!GSM) warp_store_pairs<N>(p.out + offm, Vw, a, b);
+          else store_pair<N>(p.out + off, a, b);
           // this thread alone used these spectrum columns: the next x point's Phase A for the
           // same line pair writes them without a barrier
           if (xp + gridDim.x < p.nxp) phase_a(xp + gridDim.x, pr);
