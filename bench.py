@@ -230,7 +230,8 @@ def aggregate_ranks(ms_local: float, cells: int, steps: int, dist=None, device="
 
 def time_steps(torch, s, f, dt, steps, warmup, stream, dist):
     """W untimed steps, then exactly `steps` steps between CUDA events on the solver's stream,
-    bracketed by barrier + synchronize.  Returns milliseconds."""
+    bracketed by barrier + synchronize.  Returns milliseconds and the kernels the library issued
+    for the timed steps."""
     s.step(f, dt, warmup)
     torch.cuda.synchronize()
     if dist:
@@ -238,14 +239,16 @@ def time_steps(torch, s, f, dt, steps, warmup, stream, dist):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    n0 = s.launch_count()
     e0.record(stream)
     s.step(f, dt, steps)
     e1.record(stream)
+    n1 = s.launch_count()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    return e0.elapsed_time(e1)
+    return e0.elapsed_time(e1), n1 - n0
 
 
 def time_pflow_launches(torch, s, f, dt, stream, reps):
@@ -495,12 +498,12 @@ def measure_form(torch, ch, W, prec, steps, warmup, stream, dist, sampler=None, 
         m0, en0 = s.moments(f)
         if sampler:
             sampler.start()
-        ms = time_steps(torch, s, f, W["dt"], steps, warmup, stream, dist)
+        ms, launches = time_steps(torch, s, f, W["dt"], steps, warmup, stream, dist)
         clocks = sampler.stop() if sampler else None
         m1, en1 = s.moments(f)
         ms_t, value = aggregate_ranks(ms, cells, steps, dist, "cuda")
         entry = {"value": value, "ms_per_step": ms_t / steps, "steps": steps, "warmup": warmup,
-                 "mass_drift": (m1 - m0) / m0, "energy0": en0, "energy": en1}
+                 "launches": launches, "mass_drift": (m1 - m0) / m0, "energy0": en0, "energy": en1}
         if clocks is not None:
             entry["clocks"] = clocks
         entry["pflow_ms"] = time_pflow_launches(torch, s, f, W["dt"], stream, pflow_reps)
@@ -538,7 +541,7 @@ def time_lpc1(torch, ch, W, stream, steps, warmup):
         f = new_f(torch, W, torch.float32)
         init_f(s, W, f)
         m0 = s.mass(f)
-        ms = time_steps(torch, s, f, W["dt"], steps, warmup, stream, None)
+        ms, _ = time_steps(torch, s, f, W["dt"], steps, warmup, stream, None)
         m1 = s.mass(f)
         s.close()
         del f
@@ -675,7 +678,7 @@ def run_chasm(args):
                      "flops_per_launch": flops_launch,
                      "traffic": (tr["dram_bytes_per_launch"] * cells / tr["cells"]) if tr else None},
         "e2e": e2e,
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": r32["launches"],
         "clocks": clocks,
         "cpu_baseline": base,
     }
@@ -1029,7 +1032,7 @@ def run_profile(args):
         s = make_solver(ch, W, ch.FP32_MIXED, stream)
         f = new_f(torch, W, torch.float32)
         init_f(s, W, f)
-        ms = time_steps(torch, s, f, W["dt"], args.steps, args.warmup, stream, None)
+        ms, _ = time_steps(torch, s, f, W["dt"], args.steps, args.warmup, stream, None)
         s.close()
     print(json.dumps({"profile_ms_per_step": ms / max(1, args.steps), "workload": W["name"]}))
 

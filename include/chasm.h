@@ -179,6 +179,11 @@ int chasm_sync(chasm_handle* h);
  * (quadratic potential). */
 int chasm_step(chasm_handle* h, void* f_dev, double dt, int32_t nsteps);
 
+/* Kernel launches issued on the handle's stream by chasm_step, chasm_advect and chasm_pflow
+ * since chasm_create (a replayed graph counts each kernel it holds), in *out.  EINVAL when h or
+ * out is NULL. */
+int chasm_launch_count(const chasm_handle* h, int64_t* out);
+
 /* The two substeps on their own (same layout, in place, asynchronous):
  *   chasm_advect: A(tau), any finite tau (tau = 0 is the identity up to rounding);
  *   chasm_pflow:  P(dt). */

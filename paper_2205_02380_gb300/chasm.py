@@ -85,6 +85,7 @@ _SIGS = [
     ("chasm_f_bytes", C.c_size_t, [C.c_void_p]),
     ("chasm_set_stream", C.c_int, [C.c_void_p, C.c_void_p]),
     ("chasm_sync", C.c_int, [C.c_void_p]),
+    ("chasm_launch_count", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     ("chasm_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32]),
     ("chasm_advect", C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
     ("chasm_pflow", C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
@@ -267,6 +268,12 @@ class Solver:
     def sync(self):
         """chasm_sync: wait for the handle's stream."""
         self._call(lib().chasm_sync)
+
+    def launch_count(self) -> int:
+        """chasm_launch_count: kernels issued by step / advect / pflow since creation."""
+        n = C.c_int64(0)
+        self._call(lib().chasm_launch_count, C.byref(n))
+        return n.value
 
     def step(self, f, dt, nsteps=1):
         """chasm_step: nsteps time steps of size dt on f in place (Strang or LPC1, as created);

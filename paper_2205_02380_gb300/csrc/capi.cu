@@ -32,6 +32,12 @@ int cuda_fail(Handle* H, cudaError_t e, const char* what) {
     cudaError_t _e = (call);                         \
     if (_e != cudaSuccess) return cuda_fail(H, _e, #call); \
   } while (0)
+// a kernel launch of the stepping calls, counted for chasm_launch_count
+#define CHASM_LAUNCH(H, call)                        \
+  do {                                               \
+    CHASM_CUDA(H, call);                             \
+    ++(H)->launches;                                 \
+  } while (0)
 
 bool is_finite(double v) { return std::isfinite(v); }
 
@@ -490,10 +496,11 @@ int build_potential_table(Handle* H) {
   return CHASM_OK;
 }
 
+void drop_graphs(Handle* H);
+
 void free_all(Handle* H) {
   if (H->stream) cudaStreamSynchronize(H->stream);
-  if (H->graph) cudaGraphExecDestroy(H->graph);
-  H->graph = nullptr;
+  drop_graphs(H);
   void* ptrs[] = {H->d_clos[0], H->d_clos[1], H->d_clos[2], H->d_lu[0], H->d_lu[1], H->d_lu[2],
                   H->d_pclos[0], H->d_pclos[1], H->d_pclos[2], H->d_plu[0], H->d_plu[1], H->d_plu[2],
                   H->adv.dev, H->d_T,
@@ -519,19 +526,19 @@ int do_advect(Handle* H, void* f, double tau, bool tables_ready) {
     int rc = ensure_advect_tables(H, tau);
     if (rc) return rc;
   }
-  for (int d = 0; d < 3; ++d) CHASM_CUDA(H, launch_advect_dim(*H, f, d, H->stream));
+  for (int d = 0; d < 3; ++d) CHASM_LAUNCH(H, launch_advect_dim(*H, f, d, H->stream));
   return CHASM_OK;
 }
 
 int do_pflow(Handle* H, void* f, double dt) {
   if (H->nuclei.empty()) {
     if (H->kappa == 0.0) return CHASM_OK;
-    for (int d = 0; d < 3; ++d) CHASM_CUDA(H, launch_kshift(*H, f, d, H->d_krows, H->stream));
+    for (int d = 0; d < 3; ++d) CHASM_LAUNCH(H, launch_kshift(*H, f, d, H->d_krows, H->stream));
     return CHASM_OK;
   }
   if (H->xs) {   // the four stages per x point in one launch, in place on f
     const double c[4] = {dt / 4, dt / 3, dt / 2, dt};
-    CHASM_CUDA(H, launch_theta_xs(*H, f, f, f, 4, c, H->stream));
+    CHASM_LAUNCH(H, launch_theta_xs(*H, f, f, f, 4, c, H->stream));
     return CHASM_OK;
   }
   // u <- f + (dt/s) Theta[u], s = 4, 3, 2, 1, u_0 = f; buffers f -> u0 -> u1 -> u0 -> f
@@ -542,7 +549,7 @@ int do_pflow(Handle* H, void* f, double dt) {
     double coef[kMaxNuclei];
     for (size_t a = 0; a < H->nuclei.size(); ++a)
       coef[a] = -(2.0 * H->nuclei[a].charge / (M_PI * M_PI * H->hbar)) * c;
-    CHASM_CUDA(H, launch_theta(*H, in[st], f, out[st], coef, H->stream));
+    CHASM_LAUNCH(H, launch_theta(*H, in[st], f, out[st], coef, H->stream));
   }
   return CHASM_OK;
 }
@@ -561,14 +568,14 @@ double harmonic_rho(const Handle* H) {
 // out = (base or 0) + c Theta_V[in] for either potential and either Coulomb form; in != out
 int theta_any(Handle* H, const void* in, const void* base, void* out, double c) {
   if (H->nuclei.empty()) {
-    CHASM_CUDA(H, launch_theta_harm(*H, in, base, out, c, H->stream));
+    CHASM_LAUNCH(H, launch_theta_harm(*H, in, base, out, c, H->stream));
   } else if (H->xs) {
-    CHASM_CUDA(H, launch_theta_xs(*H, in, base, out, 1, &c, H->stream));
+    CHASM_LAUNCH(H, launch_theta_xs(*H, in, base, out, 1, &c, H->stream));
   } else {
     double coef[kMaxNuclei];
     for (size_t a = 0; a < H->nuclei.size(); ++a)
       coef[a] = -(2.0 * H->nuclei[a].charge / (M_PI * M_PI * H->hbar)) * c;
-    CHASM_CUDA(H, launch_theta(*H, in, base, out, coef, H->stream));
+    CHASM_LAUNCH(H, launch_theta(*H, in, base, out, coef, H->stream));
   }
   return CHASM_OK;
 }
@@ -592,10 +599,10 @@ int issue_step_lpc1(Handle* H, void* f, double dt) {
     x.base2 = U;
     x.cbase2 = 0.5 * dt;
     const double c = 0.5 * dt;
-    CHASM_CUDA(H, launch_theta_xs(*H, f, f, f, 1, &c, H->stream, x));
+    CHASM_LAUNCH(H, launch_theta_xs(*H, f, f, f, 1, &c, H->stream, x));
     return CHASM_OK;
   }
-  CHASM_CUDA(H, launch_lpc1_combine(*H, f, U, V, dt, H->stream));
+  CHASM_LAUNCH(H, launch_lpc1_combine(*H, f, U, V, dt, H->stream));
   return theta_any(H, V, f, f, 0.5 * dt);
 }
 
@@ -628,6 +635,33 @@ int issue_step(Handle* H, void* f, double dt) {
   rc = do_pflow(H, f, dt);
   if (rc) return rc;
   return do_advect(H, f, 0.5 * dt, true);
+}
+
+void drop_graphs(Handle* H) {
+  if (H->graph) cudaGraphExecDestroy(H->graph);
+  H->graph = nullptr;
+}
+
+// Captures what issue() issues on the handle's stream into an executable graph; the kernels it
+// holds are counted in *nodes (and not in H->launches, which counts replays).
+template <class F>
+int capture(Handle* H, cudaGraphExec_t* out, int64_t* nodes, F&& issue) {
+  cudaGraph_t gr = nullptr;
+  const int64_t before = H->launches;
+  CHASM_CUDA(H, cudaStreamBeginCapture(H->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = issue();
+  cudaError_t e = cudaStreamEndCapture(H->stream, &gr);
+  *nodes = H->launches - before;
+  H->launches = before;
+  if (rc) {
+    if (gr) cudaGraphDestroy(gr);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(H, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return cuda_fail(H, e, "cudaGraphInstantiate");
+  return CHASM_OK;
 }
 
 }  // namespace
@@ -833,14 +867,18 @@ size_t chasm_f_bytes(const chasm_handle* h) {
 int chasm_set_stream(chasm_handle* h, void* stream) {
   Handle* H = reinterpret_cast<Handle*>(h);
   if (!H) return fail(nullptr, CHASM_EINVAL, "handle is NULL");
-  if (H->graph) {
-    cudaGraphExecDestroy(H->graph);
-    H->graph = nullptr;
-  }
+  drop_graphs(H);
   cudaStreamSynchronize(H->stream);
   if (H->own_stream) cudaStreamDestroy(H->stream);
   H->own_stream = false;
   H->stream = static_cast<cudaStream_t>(stream);
+  return CHASM_OK;
+}
+
+int chasm_launch_count(const chasm_handle* h, int64_t* out) {
+  const Handle* H = reinterpret_cast<const Handle*>(h);
+  if (!H || !out) return fail(nullptr, CHASM_EINVAL, "handle or out is NULL");
+  *out = H->launches;
   return CHASM_OK;
 }
 
@@ -870,26 +908,16 @@ int chasm_step(chasm_handle* h, void* f, double dt, int32_t nsteps) {
     return CHASM_OK;
   }
   if (!H->graph || H->graph_f != f || H->graph_dt != dt) {
-    if (H->graph) {
-      cudaGraphExecDestroy(H->graph);
-      H->graph = nullptr;
-    }
-    cudaGraph_t gr = nullptr;
-    CHASM_CUDA(H, cudaStreamBeginCapture(H->stream, cudaStreamCaptureModeThreadLocal));
-    rc = issue_step(H, f, dt);
-    cudaError_t e = cudaStreamEndCapture(H->stream, &gr);
-    if (rc) {
-      if (gr) cudaGraphDestroy(gr);
-      return rc;
-    }
-    if (e != cudaSuccess) return cuda_fail(H, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&H->graph, gr, 0);
-    cudaGraphDestroy(gr);
-    if (e != cudaSuccess) return cuda_fail(H, e, "cudaGraphInstantiate");
+    drop_graphs(H);
+    rc = capture(H, &H->graph, &H->graph_nodes, [&] { return issue_step(H, f, dt); });
+    if (rc) return rc;
     H->graph_f = f;
     H->graph_dt = dt;
   }
-  for (int i = 0; i < nsteps; ++i) CHASM_CUDA(H, cudaGraphLaunch(H->graph, H->stream));
+  for (int i = 0; i < nsteps; ++i) {
+    CHASM_CUDA(H, cudaGraphLaunch(H->graph, H->stream));
+    H->launches += H->graph_nodes;
+  }
   return CHASM_OK;
 }
 

@@ -191,10 +191,12 @@ struct Handle {
   double* d_diag = nullptr;        // diagnostics: per-x partial sums and the result
   // host-buffer entry point
   void* d_fhost = nullptr;
-  // step graph cache
+  // step graph cache (one Strang or LPC1 step) and the kernel launches it holds
   cudaGraphExec_t graph = nullptr;
+  int64_t graph_nodes = 0;
   void* graph_f = nullptr;
   double graph_dt = 0.0;
+  int64_t launches = 0;            // kernels issued by the stepping calls (chasm_launch_count)
 
   std::string err;
   size_t workspace = 0;

@@ -170,10 +170,10 @@ __device__ __forceinline__ void line_setup(const AdvParams<T>& p, int64_t line, 
 }
 
 // ---- register kernel ----
-template <typename T, int NX, int S>
-__device__ __forceinline__ void eval_store(const T (&v)[NX + 2], T w0, T w1, T w2, T w3, T* src,
-                                           int64_t s_d) {
-  // out_j = w0 eta_{j-S-2} + w1 eta_{j-S-1} + w2 eta_{j-S} + w3 eta_{j-S+1}; slot of eta_nu = nu+1
+// out_j = w0 eta_{j-S-2} + w1 eta_{j-S-1} + w2 eta_{j-S} + w3 eta_{j-S+1}; slot of eta_nu = nu+1.
+// st(j, out_j) writes the result (global memory or a shared-memory tile).
+template <typename T, int NX, int S, class St>
+__device__ __forceinline__ void eval_line(const T (&v)[NX + 2], T w0, T w1, T w2, T w3, St&& st) {
 #pragma unroll
   for (int j = 0; j < NX; ++j) {
     T acc = (T)0;
@@ -182,15 +182,15 @@ __device__ __forceinline__ void eval_store(const T (&v)[NX + 2], T w0, T w1, T w
     if (s0 + 1 >= 0 && s0 + 1 <= NX + 1) acc = fma(w1, v[s0 + 1], acc);
     if (s0 + 2 >= 0 && s0 + 2 <= NX + 1) acc = fma(w2, v[s0 + 2], acc);
     if (s0 + 3 >= 0 && s0 + 3 <= NX + 1) acc = fma(w3, v[s0 + 3], acc);
-    src[(int64_t)j * s_d] = acc;
+    st(j, acc);
   }
 }
 
-// One line in registers: closure, Thomas sweep, ghosts, 4-tap evaluation and store.  JC: the
-// number of closure taps evaluated (the stencil is zero beyond the launch's J <= JC).
+// One line in registers: closure, Thomas sweep and ghosts; v holds the spline coefficients
+// eta_{-1..N+1} afterwards.  JC: the number of closure taps evaluated (the stencil is zero beyond
+// the launch's J <= JC).
 template <typename T, int NX, int JC>
-__device__ __forceinline__ void solve_eval_line(const AdvParams<T>& p, const AdvTabs<T>& tb,
-                                                T (&v)[NX + 2], int kd, T* dst, int64_t s_d) {
+__device__ __forceinline__ void solve_line(const AdvParams<T>& p, const AdvTabs<T>& tb, T (&v)[NX + 2]) {
   constexpr int N = NX - 1;
   Closure<T> cl;
 #pragma unroll
@@ -209,15 +209,21 @@ __device__ __forceinline__ void solve_eval_line(const AdvParams<T>& p, const Adv
   for (int i = N - 1; i >= 0; --i) v[i + 1] = v[i + 1] - tb.lu[0][i] * v[i + 2];
   v[0] = (T)cl.gl(v[2], h2val(p));
   v[N + 2] = (T)cl.gr(v[N], h2val(p));
+}
 
+// solve_line, then the 4-tap evaluation at the feet of line k index kd, written by st
+template <typename T, int NX, int JC, class St>
+__device__ __forceinline__ void solve_eval_line(const AdvParams<T>& p, const AdvTabs<T>& tb,
+                                                T (&v)[NX + 2], int kd, St&& st) {
+  solve_line<T, NX, JC>(p, tb, v);
   const int sh = __ldg(p.ns + kd);
   const T w0 = __ldg(p.w + 4 * kd + 0), w1 = __ldg(p.w + 4 * kd + 1);
   const T w2 = __ldg(p.w + 4 * kd + 2), w3 = __ldg(p.w + 4 * kd + 3);
   switch (sh) {
-    case -2: eval_store<T, NX, -2>(v, w0, w1, w2, w3, dst, s_d); break;
-    case -1: eval_store<T, NX, -1>(v, w0, w1, w2, w3, dst, s_d); break;
-    case 0: eval_store<T, NX, 0>(v, w0, w1, w2, w3, dst, s_d); break;
-    default: eval_store<T, NX, 1>(v, w0, w1, w2, w3, dst, s_d); break;
+    case -2: eval_line<T, NX, -2>(v, w0, w1, w2, w3, st); break;
+    case -1: eval_line<T, NX, -1>(v, w0, w1, w2, w3, st); break;
+    case 0: eval_line<T, NX, 0>(v, w0, w1, w2, w3, st); break;
+    default: eval_line<T, NX, 1>(v, w0, w1, w2, w3, st); break;
   }
 }
 
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p, c
     T v[NX + 2];   // slot nu + 1 holds eta_nu (phi_j before the solve)
 #pragma unroll
     for (int j = 0; j < NX; ++j) v[j + 1] = src[(int64_t)j * p.s_d];
-    solve_eval_line<T, NX, JC>(p, tb, v, kd, src, p.s_d);
+    solve_eval_line<T, NX, JC>(p, tb, v, kd, [&](int j, T o) { src[(int64_t)j * p.s_d] = o; });
   } else {
     T v0[NX + 2], v1[NX + 2];
 #pragma unroll
@@ -248,8 +254,8 @@ __global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p, c
     int kd1;
     T* src1;
     line_setup(p, t * LPT + 1, src1, kd1);
-    solve_eval_line<T, NX, JC>(p, tb, v0, kd, src, p.s_d);
-    solve_eval_line<T, NX, JC>(p, tb, v1, kd1, src1, p.s_d);
+    solve_eval_line<T, NX, JC>(p, tb, v0, kd, [&](int j, T o) { src[(int64_t)j * p.s_d] = o; });
+    solve_eval_line<T, NX, JC>(p, tb, v1, kd1, [&](int j, T o) { src1[(int64_t)j * p.s_d] = o; });
   }
 }
 
@@ -405,7 +411,7 @@ __global__ void __launch_bounds__(kAdvectThreads) k_advect_patches(AdvParams<T> 
 }
 
 template <typename T>
-cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
+AdvParams<T> make_params(const Handle& H, void* f, int dim) {
   const GridDesc& g = H.g;
   AdvParams<T> p;
   p.f = static_cast<T*>(f);
@@ -431,6 +437,43 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
   const T* wbase = static_cast<const T*>(H.adv.dev);
   p.w = wbase + (size_t)dim * g.nk * 4;
   p.ns = reinterpret_cast<const int*>(wbase + (size_t)3 * g.nk * 4) + dim * g.nk;
+  return p;
+}
+
+// closure stencils and Thomas factors of dimension dim for the register kernels
+template <typename T>
+AdvTabs<T> make_tabs(const Handle& H, int dim) {
+  const int n = H.g.nx[dim];
+  AdvTabs<T> tb;
+  std::memset(&tb, 0, sizeof(tb));
+  const std::vector<double>& hc = H.h_clos[dim];
+  const std::vector<double>& hl = H.h_lu[dim];
+  for (int j = 0; j < n; ++j) {
+    if constexpr (sizeof(T) == 4) {   // unevaluated float pairs hi + lo of the FP64 stencils
+      tb.c[0][j] = (float)hc[j];
+      tb.c[1][j] = (float)(hc[j] - (double)tb.c[0][j]);
+      tb.c[2][j] = (float)hc[n + j];
+      tb.c[3][j] = (float)(hc[n + j] - (double)tb.c[2][j]);
+    } else {
+      tb.c[0][j] = hc[j];
+      tb.c[1][j] = hc[n + j];
+    }
+    tb.lu[0][j] = (T)hl[j];
+    tb.lu[1][j] = (T)hl[n + j];
+  }
+  return tb;
+}
+
+// the register kernels apply: integer shifts in [-2, 1] and a compiled line length
+bool reg_applies(const Handle& H, int dim) {
+  return H.adv.ns_min[dim] >= -2 && H.adv.ns_max[dim] <= 1 && H.opt.patches[dim] <= 1 &&
+         H.g.nx[dim] <= kRegMaxNx;
+}
+
+template <typename T>
+cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
+  const GridDesc& g = H.g;
+  AdvParams<T> p = make_params<T>(H, f, dim);
   const int B = kAdvectThreads;
   const int P = H.opt.patches[dim];
   if (P > 1) {
@@ -447,27 +490,10 @@ cudaError_t launch_t(const Handle& H, void* f, int dim, cudaStream_t s) {
     k_advect_patches<T><<<(unsigned)((p.n_lines + Bp - 1) / Bp), Bp, elems * Bp * sizeof(T), s>>>(p, q);
     return cudaGetLastError();
   }
-  const bool reg_shift = H.adv.ns_min[dim] >= -2 && H.adv.ns_max[dim] <= 1;
-  if (reg_shift && p.n <= kRegMaxNx) {
+  if (reg_applies(H, dim)) {
     const int64_t lpt = sizeof(T) == 4 ? 2 : 1;   // kvol = nk^3 is even
     const unsigned rblocks = (unsigned)((p.n_lines / lpt + B - 1) / B);
-    AdvTabs<T> tb;
-    std::memset(&tb, 0, sizeof(tb));
-    const std::vector<double>& hc = H.h_clos[dim];
-    const std::vector<double>& hl = H.h_lu[dim];
-    for (int j = 0; j < p.n; ++j) {
-      if constexpr (sizeof(T) == 4) {   // unevaluated float pairs hi + lo of the FP64 stencils
-        tb.c[0][j] = (float)hc[j];
-        tb.c[1][j] = (float)(hc[j] - (double)tb.c[0][j]);
-        tb.c[2][j] = (float)hc[p.n + j];
-        tb.c[3][j] = (float)(hc[p.n + j] - (double)tb.c[2][j]);
-      } else {
-        tb.c[0][j] = hc[j];
-        tb.c[1][j] = hc[p.n + j];
-      }
-      tb.lu[0][j] = (T)hl[j];
-      tb.lu[1][j] = (T)hl[p.n + j];
-    }
+    const AdvTabs<T> tb = make_tabs<T>(H, dim);
     // closure taps: the launch's J rounded up to a compiled bucket (the stencil is zero beyond J)
     const bool short_j = p.J <= 24 && p.n > 24;
 #define CHASM_REG(NX)                                                                   \

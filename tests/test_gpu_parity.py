@@ -346,3 +346,24 @@ def test_zero_data_and_zero_steps(ch, name):
         s.sync()
         assert int(torch.count_nonzero(z)) == 0
         assert torch.equal(f, before)
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_launch_count_counts_the_step_kernels(ch, graphs):
+    """chasm_launch_count: a Strang step is 6 advection passes and one P(dt) launch in the table
+    form (P(dt) as four Theta launches in the modulated form); a graph replay counts its kernels;
+    an LPC1 step in the table form is Theta, two advections and the corrector launch."""
+    prob = problem((6, 5, 7), 8, -3.0, 3.0, 3.0, nuclei=[((0.1, 0.0, 0.2), 1.0)])
+    f0 = rough_input(prob, 23)
+    cases = [("table", ch.STRANG, 7), ("modulated", ch.STRANG, 10), ("table", ch.LPC1, 8)]
+    for form, integ, per_step in cases:
+        with solver(ch, prob, "fp32", form, use_graphs=graphs, integrator=integ) as s:
+            f = to_dev(f0, "fp32")
+            for n in (1, 3):
+                c0 = s.launch_count()
+                s.step(f, 0.02, n)
+                assert s.launch_count() - c0 == per_step * n, (form, integ, n)
+            c0 = s.launch_count()
+            s.advect(f, 0.01)
+            assert s.launch_count() - c0 == 3
+            s.sync()
