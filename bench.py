@@ -1053,6 +1053,7 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="FP32 timed steps only (no FP64, e2e, baseline or clocks): for ncu captures")
     ap.add_argument("--nx", type=int, default=None, help="override N_x (profiling on smaller cases)")
+    ap.add_argument("--nk", type=int, default=None, help="override N_k (profiling on smaller cases)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-lpc1", action="store_true")
     ap.add_argument("--bench-serve-requests", type=int, default=8)
@@ -1079,6 +1080,11 @@ def main():
         old = f"{W['nx']}^3x"
         W["nx"] = args.nx
         W["name"] = W["name"].replace(old, f"{args.nx}^3x")
+    if args.nk:
+        W = WORKLOADS[args.workload]
+        old = f"x{W['nk']}^3"
+        W["nk"] = args.nk
+        W["name"] = W["name"].replace(old, f"x{args.nk}^3")
     if args.profile:
         run_profile(args)
         return

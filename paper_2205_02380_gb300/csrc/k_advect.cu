@@ -211,6 +211,35 @@ __device__ __forceinline__ void solve_line(const AdvParams<T>& p, const AdvTabs<
   v[N + 2] = (T)cl.gr(v[N], h2val(p));
 }
 
+// the 4-tap evaluation of two lines with the same integer shift S (weights wa, wb), written
+// together by st(j, out_a, out_b)
+template <typename T, int NX, int S, class St>
+__device__ __forceinline__ void eval_line2(const T (&va)[NX + 2], const T (&vb)[NX + 2], const T (&wa)[4],
+                                           const T (&wb)[4], St&& st) {
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    T a = (T)0, b = (T)0;
+    const int s0 = j - S - 1;
+    if (s0 >= 0 && s0 <= NX + 1) {
+      a = wa[0] * va[s0];
+      b = wb[0] * vb[s0];
+    }
+    if (s0 + 1 >= 0 && s0 + 1 <= NX + 1) {
+      a = fma(wa[1], va[s0 + 1], a);
+      b = fma(wb[1], vb[s0 + 1], b);
+    }
+    if (s0 + 2 >= 0 && s0 + 2 <= NX + 1) {
+      a = fma(wa[2], va[s0 + 2], a);
+      b = fma(wb[2], vb[s0 + 2], b);
+    }
+    if (s0 + 3 >= 0 && s0 + 3 <= NX + 1) {
+      a = fma(wa[3], va[s0 + 3], a);
+      b = fma(wb[3], vb[s0 + 3], b);
+    }
+    st(j, a, b);
+  }
+}
+
 // solve_line, then the 4-tap evaluation at the feet of line k index kd, written by st
 template <typename T, int NX, int JC, class St>
 __device__ __forceinline__ void solve_eval_line(const AdvParams<T>& p, const AdvTabs<T>& tb,
@@ -229,7 +258,8 @@ __device__ __forceinline__ void solve_eval_line(const AdvParams<T>& p, const Adv
 
 // FP64 form: one line per thread.  FP32-mixed form: two adjacent k (lines l and l + 1 share the
 // x indices) per thread, loaded with 8-byte accesses so each thread keeps twice the bytes in
-// flight.
+// flight, and stored with 8-byte accesses when both lines have the same integer shift (always
+// for the x1 and x2 passes, whose shift depends on k1 or k2 only).
 template <typename T, int NX, int JC>
 __global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p, const AdvTabs<T> tb) {
   constexpr int LPT = sizeof(T) == 4 ? 2 : 1;
@@ -254,8 +284,27 @@ __global__ void __launch_bounds__(kAdvectThreads) k_advect_reg(AdvParams<T> p, c
     int kd1;
     T* src1;
     line_setup(p, t * LPT + 1, src1, kd1);
-    solve_eval_line<T, NX, JC>(p, tb, v0, kd, [&](int j, T o) { src[(int64_t)j * p.s_d] = o; });
-    solve_eval_line<T, NX, JC>(p, tb, v1, kd1, [&](int j, T o) { src1[(int64_t)j * p.s_d] = o; });
+    const int sh0 = __ldg(p.ns + kd), sh1 = __ldg(p.ns + kd1);
+    if (sh0 != sh1) {   // rare: the two k straddle an integer shift
+      solve_eval_line<T, NX, JC>(p, tb, v0, kd, [&](int j, T o) { src[(int64_t)j * p.s_d] = o; });
+      solve_eval_line<T, NX, JC>(p, tb, v1, kd1, [&](int j, T o) { src1[(int64_t)j * p.s_d] = o; });
+      return;
+    }
+    solve_line<T, NX, JC>(p, tb, v0);
+    solve_line<T, NX, JC>(p, tb, v1);
+    T wa[4], wb[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      wa[c] = __ldg(p.w + 4 * kd + c);
+      wb[c] = __ldg(p.w + 4 * kd1 + c);
+    }
+    auto st = [&](int j, T a, T b) { *reinterpret_cast<float2*>(src + (int64_t)j * p.s_d) = make_float2(a, b); };
+    switch (sh0) {
+      case -2: eval_line2<T, NX, -2>(v0, v1, wa, wb, st); break;
+      case -1: eval_line2<T, NX, -1>(v0, v1, wa, wb, st); break;
+      case 0: eval_line2<T, NX, 0>(v0, v1, wa, wb, st); break;
+      default: eval_line2<T, NX, 1>(v0, v1, wa, wb, st); break;
+    }
   }
 }
 
