@@ -257,7 +257,9 @@ int chasm_moments_noalloc(const void* f_dev, const chasm_grid* grid, const chasm
                           void* cuda_stream, double* mass, double* energy);
 
 /* Initial data written on the GPU (asynchronous):
- *   chasm_init_gaussians: f = sum_i w_i exp(-ax_i |x - x0_i|^2 - ak_i |k - k0_i|^2), n >= 1;
+ *   chasm_init_gaussians: f = sum_i w_i exp(-ax_i |x - x0_i|^2 - ak_i |k - k0_i|^2), 1 <= n <=
+ *     16, evaluated in FP64 as products of the per-dimension factors and rounded to the storage
+ *     type; f_dev 16-byte aligned (EINVAL otherwise);
  *   chasm_init_hydrogen_1s: the 1s Wigner function of phi = exp(-|x - c|)/(2 sqrt(2) pi^2) by
  *     the discrete Fourier sum of Sec. 5.2 with n_y samples per dimension (n_y a multiple of
  *     2 N_k, at most 256), dy = 2 pi / (N_k dk), computed in FP64 and rounded to the storage

@@ -1054,6 +1054,7 @@ int chasm_init_gaussians(chasm_handle* h, void* f, const chasm_gaussian* g, int3
   Handle* H = reinterpret_cast<Handle*>(h);
   if (!H) return fail(nullptr, CHASM_EINVAL, "handle is NULL");
   if (!f || !g) return fail(H, CHASM_EINVAL, "f/g is NULL");
+  if ((reinterpret_cast<uintptr_t>(f) & 15) != 0) return fail(H, CHASM_EINVAL, "f must be 16-byte aligned");
   if (n < 1 || n > 16) return fail(H, CHASM_EINVAL, "n must be in [1, 16]");
   for (int i = 0; i < n; ++i)
     if (!is_finite(g[i].w) || !is_finite(g[i].ax) || !is_finite(g[i].ak) || g[i].ax < 0 || g[i].ak < 0)

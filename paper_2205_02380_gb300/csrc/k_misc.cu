@@ -218,29 +218,52 @@ struct Packets {
   chasm_gaussian g[16];
 };
 
+// Each packet factorises, w exp(-ax |x - x0|^2) exp(-ak |k - k0|^2) = w prod_d gx_d(x_d) prod_d
+// gk_d(k_d), so one block per x point forms w prod_d gx_d once per packet and the 1-D k factors
+// gk_d (3 N_k per packet) in shared memory; every cell is then three FP64 products per packet,
+// summed in FP64 and rounded once to T.  The threads write four consecutive k3 values each.
+constexpr int kInitThreads = 256;
+
 template <typename T>
-__global__ void k_init_gauss(T* __restrict__ f, GridDesc gd, Packets P) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= gd.ncell) return;
-  const int nk = gd.nk;
-  const int64_t xp = i / gd.kvol;
-  const int e = (int)(i % gd.kvol);
-  const int i3 = (int)(xp % gd.nx[2]), i2 = (int)((xp / gd.nx[2]) % gd.nx[1]);
-  const int i1 = (int)(xp / ((int64_t)gd.nx[2] * gd.nx[1]));
-  const double x[3] = {gd.x_lo[0] + i1 * gd.h[0], gd.x_lo[1] + i2 * gd.h[1], gd.x_lo[2] + i3 * gd.h[2]};
-  const double k[3] = {(e / (nk * nk) - nk / 2) * gd.dk, ((e / nk) % nk - nk / 2) * gd.dk,
-                       (e % nk - nk / 2) * gd.dk};
-  double s = 0.0;
-  for (int p = 0; p < P.n; ++p) {
-    const chasm_gaussian& g = P.g[p];
-    double rx = 0.0, rk = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      rx += (x[d] - g.x0[d]) * (x[d] - g.x0[d]);
-      rk += (k[d] - g.k0[d]) * (k[d] - g.k0[d]);
-    }
-    s += g.w * exp(-g.ax * rx - g.ak * rk);
+__global__ void __launch_bounds__(kInitThreads) k_init_gauss(T* __restrict__ f, GridDesc gd, Packets P) {
+  __shared__ double gk[16][3][32];   // gk[p][d][j] = exp(-ak (k_j - k0_d)^2)
+  __shared__ double wx[16];          // w prod_d exp(-ax (x_d - x0_d)^2)
+  const int nk = gd.nk, tid = threadIdx.x;
+  int lg = 0;
+  while ((1 << lg) < nk) ++lg;   // nk = 2^lg
+  for (int i = tid; i < P.n * 3 * nk; i += blockDim.x) {
+    const int p = i / (3 * nk), d = (i / nk) % 3, j = i % nk;
+    const double k = (j - nk / 2) * gd.dk - P.g[p].k0[d];
+    gk[p][d][j] = exp(-P.g[p].ak * k * k);
   }
-  f[i] = (T)s;
+  for (int64_t xp = blockIdx.x; xp < gd.nxp; xp += gridDim.x) {
+    __syncthreads();   // gk written; the previous x point's wx read
+    if (tid < P.n) {
+      const int i3 = (int)(xp % gd.nx[2]), i2 = (int)((xp / gd.nx[2]) % gd.nx[1]);
+      const int i1 = (int)(xp / ((int64_t)gd.nx[2] * gd.nx[1]));
+      const chasm_gaussian& g = P.g[tid];
+      const double dx[3] = {gd.x_lo[0] + i1 * gd.h[0] - g.x0[0], gd.x_lo[1] + i2 * gd.h[1] - g.x0[1],
+                            gd.x_lo[2] + i3 * gd.h[2] - g.x0[2]};
+      wx[tid] = g.w * (exp(-g.ax * dx[0] * dx[0]) * exp(-g.ax * dx[1] * dx[1]) * exp(-g.ax * dx[2] * dx[2]));
+    }
+    __syncthreads();
+    T* fx = f + xp * gd.kvol;
+    for (int e0 = 4 * tid; e0 < gd.kvol; e0 += 4 * blockDim.x) {   // kvol = nk^3 is a multiple of 4
+      const int k1 = e0 >> (2 * lg), k2 = (e0 >> lg) & (nk - 1), k3 = e0 & (nk - 1);
+      double s[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int p = 0; p < P.n; ++p) {
+        const double a = wx[p] * (gk[p][0][k1] * gk[p][1][k2]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s[c] = fma(a, gk[p][2][k3 + c], s[c]);
+      }
+      if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(fx + e0) = make_float4((float)s[0], (float)s[1], (float)s[2], (float)s[3]);
+      } else {
+        reinterpret_cast<double2*>(fx + e0)[0] = make_double2(s[0], s[1]);
+        reinterpret_cast<double2*>(fx + e0)[1] = make_double2(s[2], s[3]);
+      }
+    }
+  }
 }
 
 // Hydrogen 1s Wigner function, discrete Fourier sum of Sec. 5.2.  Because dk dy = 2 pi / N the
@@ -386,11 +409,11 @@ cudaError_t launch_init_gaussians(const Handle& H, void* f, const chasm_gaussian
   Packets P;
   P.n = n;
   for (int i = 0; i < n; ++i) P.g[i] = g[i];
-  const unsigned nb = nblk(H.g.ncell, 256);
+  const unsigned nb = (unsigned)std::min<int64_t>(H.g.nxp, (int64_t)H.num_sms * 8);
   if (H.fp64)
-    k_init_gauss<double><<<nb, 256, 0, s>>>((double*)f, H.g, P);
+    k_init_gauss<double><<<nb, kInitThreads, 0, s>>>((double*)f, H.g, P);
   else
-    k_init_gauss<float><<<nb, 256, 0, s>>>((float*)f, H.g, P);
+    k_init_gauss<float><<<nb, kInitThreads, 0, s>>>((float*)f, H.g, P);
   return cudaGetLastError();
 }
 

@@ -210,9 +210,13 @@ def test_moments_match_oracle_and_are_reproducible(ch, name):
 
 
 @pytest.mark.parametrize("name", ["fp64", "fp32"])
-def test_init_gaussians_matches_generator(ch, name):
-    prob = problem((5, 6, 7), 8, -3.0, 3.0, 3.0)
+@pytest.mark.parametrize("nk,npk", [(8, 2), (16, 5), (32, 16)])
+def test_init_gaussians_matches_generator(ch, name, nk, npk):
+    prob = problem((5, 6, 7) if nk < 32 else (4, 5, 4), nk, -3.0, 3.0, 3.0)
+    rng = np.random.default_rng(nk + npk)
     pk = [synth.packet((0.5, -0.2, 0.1), (0.3, 0.0, -0.2)), synth.packet((-1, 1, 0), (0, 0, 0.5))]
+    pk += [synth.packet(rng.uniform(-2, 2, 3), rng.uniform(-1, 1, 3), ax=rng.uniform(0.2, 1.0),
+                        ak=rng.uniform(0.5, 3.0), w=rng.uniform(-0.5, 1.0)) for _ in range(npk - 2)]
     with solver(ch, prob, name) as s:
         f = torch.empty(prob.shape, device="cuda", dtype=dtype(name))
         s.init_gaussians(f, pk)
