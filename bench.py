@@ -642,8 +642,9 @@ def run_chasm(args):
     try:
         fma32, fma64 = ch.chasm.fma_peaks()
         fma32x2 = ch.chasm.fma_peak_f32x2()
+        fft_only = ch.chasm.fft_pk_rate() if nk == 32 else None
     except Exception:
-        fma32 = fma64 = fma32x2 = None
+        fma32 = fma64 = fma32x2 = fft_only = None
     tr = committed_traffic()
     e2e = r32.pop("e2e")
     line = {
@@ -674,6 +675,8 @@ def run_chasm(args):
                      "measured_fma_peak_tflops": fma32,
                      "frac_of_measured_fma_peak": (achieved / fma32) if fma32 else None,
                      "measured_packed_f32x2_fma_tflops": fma32x2,
+                     "fft_only_tflops": fft_only,
+                     "frac_of_fft_only": (achieved / fft_only) if fft_only else None,
                      "ms_per_launch": r32["pflow_ms"],
                      "flops_per_launch": flops_launch,
                      "traffic": (tr["dram_bytes_per_launch"] * cells / tr["cells"]) if tr else None},

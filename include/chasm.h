@@ -235,6 +235,13 @@ int chasm_fma_peaks(double* fp32_tflops, double* fp64_tflops);
  * raise the FP32 arithmetic ceiling or only halve the instructions issued.  Synchronous. */
 int chasm_fma_peak_f32x2(double* tflops);
 
+/* The register FFT of the FP32 table-form P(dt) kernel (N_k = 32) alone, in that kernel's CTA
+ * shape (256 threads, one CTA per SM): forward and inverse packed 32-point FFTs on register data,
+ * no memory traffic, flops counted as the kernel's roofline counts them (5 n log2 n per complex
+ * length-n FFT), in TFLOP/s.  The ceiling of FFT arithmetic at that occupancy, beside the FMA
+ * peaks above.  Synchronous. */
+int chasm_fft_pk_rate(double* tflops);
+
 /* Mass and energy exactly as chasm_moments defines them, for callers that cannot allocate
  * device memory when they need them: services that hand their whole device-memory budget to
  * solves up front (an allocation for a check could then fail or push the device past the budget)

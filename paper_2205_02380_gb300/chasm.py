@@ -99,6 +99,7 @@ _SIGS = [
     ("chasm_expectations", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     ("chasm_fma_peaks", C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("chasm_fma_peak_f32x2", C.c_int, [C.POINTER(C.c_double)]),
+    ("chasm_fft_pk_rate", C.c_int, [C.POINTER(C.c_double)]),
     ("chasm_moments_noalloc", C.c_int, [C.c_void_p, C.POINTER(Grid), C.POINTER(Box), C.POINTER(Potential),
                                         C.c_double, C.c_double, C.c_int32, C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -452,4 +453,11 @@ def fma_peak_f32x2():
     """Packed single-precision FMA throughput in TFLOP/s (chasm_fma_peak_f32x2)."""
     a = C.c_double()
     _check(lib().chasm_fma_peak_f32x2(C.byref(a)))
+    return a.value
+
+
+def fft_pk_rate():
+    """Algorithmic TFLOP/s of the P(dt) kernel's register FFT alone (chasm_fft_pk_rate)."""
+    a = C.c_double()
+    _check(lib().chasm_fft_pk_rate(C.byref(a)))
     return a.value

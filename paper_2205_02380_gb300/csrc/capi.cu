@@ -1040,6 +1040,14 @@ int chasm_fma_peak_f32x2(double* tflops) {
   return CHASM_OK;
 }
 
+int chasm_fft_pk_rate(double* tflops) {
+  if (!tflops) return fail(nullptr, CHASM_EINVAL, "output is NULL");
+  const cudaError_t e = measure_fft_pk_rate(tflops);
+  if (e != cudaSuccess)
+    return fail(nullptr, CHASM_ECUDA, std::string("chasm_fft_pk_rate: ") + cudaGetErrorString(e));
+  return CHASM_OK;
+}
+
 int chasm_mass(chasm_handle* h, const void* f, double* out) {
   if (!out) return fail(reinterpret_cast<Handle*>(h), CHASM_EINVAL, "out is NULL");
   return chasm_moments(h, f, out, nullptr);

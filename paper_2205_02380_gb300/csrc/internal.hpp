@@ -97,6 +97,7 @@ cudaError_t launch_diag(const Handle& H, const void* f, int what, int j, double*
 // SIMT FMA throughput of the current device in TFLOP/s (k_peak.cu); either pointer may be null
 cudaError_t measure_fma_peaks(double* fp32_tflops, double* fp64_tflops);
 cudaError_t measure_fma_peak_f32x2(double* tflops);
+cudaError_t measure_fft_pk_rate(double* tflops);
 // the per-x symbol table (k_xsym.cu), [nxp][N][2N][2N] in the storage type; needs H.d_T
 size_t xs_table_bytes(int nk, int64_t nxp, size_t elt);
 cudaError_t build_xs_table(const Handle& H, void* sig, cudaStream_t s);
