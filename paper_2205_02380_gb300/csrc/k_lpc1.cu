@@ -4,9 +4,10 @@
 //                   out = (base or out) + coef kappa (x_d - c_d)/hbar D u along k_d, where D is the
 //                   spectral derivative on the periodic k-grid (i xi_m, xi_m = pi m / L_k, the
 //                   Nyquist mode dropped), applied as its circulant: (D u)_p = sum_j d_j u_{p-j},
-//                   d_j = -(2/N) sum_{m=1}^{N/2-1} xi_m sin(2 pi m j / N).  One thread per k-line,
-//                   the N taps in the kernel's parameter block (constant-bank operands); the
-//                   k3 pass (k_kderiv3) stages its contiguous lines in shared memory.
+//                   d_j = -(2/N) sum_{m=1}^{N/2-1} xi_m sin(2 pi m j / N).  One thread per k-line
+//                   (two k-adjacent lines in FP32), the N taps in the kernel's parameter block
+//                   (constant-bank operands); the k3 pass (k_kderiv3) stages its contiguous
+//                   lines in shared memory.
 //   k_lpc1_combine  predictor and corrector base from the advected fields g = f(A_dt) and
 //                   h = Theta[f](A_dt): v = g + dt h (the predictor f~), f = g + dt/2 h.
 #include "internal.hpp"
@@ -28,9 +29,12 @@ struct KDerivParams {
   T d[N];
 };
 
+// FP64: one line per thread.  FP32: two lines per thread, k-adjacent in memory (r even and r + 1,
+// the same x point), moved with 8-byte accesses.
 template <typename T, int N>
 __global__ void __launch_bounds__(128) k_kderiv(const KDerivParams<T, N> p) {
-  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int LPT = sizeof(T) == 4 ? 2 : 1;
+  const int64_t line = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * LPT;
   if (line >= p.nxp * N * N) return;
   const int64_t xp = line / (N * N);
   const int r = (int)(line % (N * N));
@@ -50,21 +54,46 @@ __global__ void __launch_bounds__(128) k_kderiv(const KDerivParams<T, N> p) {
     id = (int)(xp % p.nx3);
   }
   const T scale = (T)(p.rate_scale * (p.x_lo + id * p.h - p.center)) * p.coef;
-  T v[N];
+  if constexpr (LPT == 1) {
+    T v[N];
 #pragma unroll
-  for (int l = 0; l < N; ++l) v[l] = p.in[base + l * stride];
+    for (int l = 0; l < N; ++l) v[l] = p.in[base + l * stride];
 #pragma unroll
-  for (int q = 0; q < N; ++q) {
-    T acc = (T)0;
+    for (int q = 0; q < N; ++q) {
+      T acc = (T)0;
 #pragma unroll
-    for (int l = 0; l < N; ++l) acc = fma(p.d[(q - l + N) & (N - 1)], v[l], acc);
-    const int64_t o = base + q * stride;
-    T b = (T)0;
-    if (p.accumulate)
-      b = p.out[o];
-    else if (p.base)
-      b = p.base[o];
-    p.out[o] = fma(scale, acc, b);
+      for (int l = 0; l < N; ++l) acc = fma(p.d[(q - l + N) & (N - 1)], v[l], acc);
+      const int64_t o = base + q * stride;
+      T b = (T)0;
+      if (p.accumulate)
+        b = p.out[o];
+      else if (p.base)
+        b = p.base[o];
+      p.out[o] = fma(scale, acc, b);
+    }
+  } else {
+    // the lines and the terms they are added to, all loads in flight before the arithmetic
+    T v0[N], v1[N];
+    float2 b[N];
+    const T* add = p.accumulate ? p.out : p.base;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const float2 u = *reinterpret_cast<const float2*>(p.in + base + l * stride);
+      v0[l] = u.x;
+      v1[l] = u.y;
+      b[l] = add ? *reinterpret_cast<const float2*>(add + base + l * stride) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T a0 = (T)0, a1 = (T)0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        a0 = fma(p.d[(q - l + N) & (N - 1)], v0[l], a0);
+        a1 = fma(p.d[(q - l + N) & (N - 1)], v1[l], a1);
+      }
+      *reinterpret_cast<float2*>(p.out + base + q * stride) =
+          make_float2(fma(scale, a0, b[q].x), fma(scale, a1, b[q].y));
+    }
   }
 }
 
@@ -153,7 +182,7 @@ cudaError_t kderiv_tn(const Handle& H, const void* in, const void* base, void* o
       acc += (M_PI * m / H.g.lk) * std::sin(2.0 * M_PI * m * j / N);
     p.d[j] = (T)(-2.0 * acc / N);
   }
-  const unsigned nb = nblk(H.g.nxp * N * N, 128);
+  const unsigned nb = nblk(H.g.nxp * N * N / (sizeof(T) == 4 ? 2 : 1), 128);   // lines per thread
   for (int d = 0; d < 3; ++d) {
     p.dim = d;
     p.accumulate = d > 0;

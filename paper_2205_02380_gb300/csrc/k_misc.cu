@@ -136,10 +136,15 @@ __global__ void k_moments_final(const double* __restrict__ partials, int nblocks
 // matrix whose first column c[q] = (1/N) sum_m phi_m e^{2 pi i m q / N} is tabulated per x_d on
 // the host; one thread applies it to one k-line in registers.
 // ---------------------------------------------------------------------------------------------
+// FP64: one line per thread.  FP32: two lines per thread, k-adjacent in memory (r even and r + 1,
+// the same x point), moved with 8-byte accesses, at three 128-thread CTAs per SM (a register bound
+// that spills a few coefficients but keeps 12 warps per SM: 6.25 -> 5.40 ms for the three passes
+// at 32^3 x 32^3).
 template <typename T, int N>
-__global__ void k_kshift(T* __restrict__ f, int64_t nxp, int nx1, int nx2, int nx3, int dim,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1) k_kshift(T* __restrict__ f, int64_t nxp, int nx1, int nx2, int nx3, int dim,
                          const T* __restrict__ rows) {
-  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int LPT = sizeof(T) == 4 ? 2 : 1;
+  const int64_t line = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * LPT;
   if (line >= nxp * N * N) return;
   const int64_t xp = line / (N * N);
   const int r = (int)(line % (N * N));
@@ -159,17 +164,38 @@ __global__ void k_kshift(T* __restrict__ f, int64_t nxp, int nx1, int nx2, int n
     id = nx1 + nx2 + (int)(xp % nx3);
   }
   const T* crow = rows + (int64_t)id * N;
-  T c[N], v[N];
+  T c[N];
 #pragma unroll
   for (int q = 0; q < N; ++q) c[q] = __ldg(crow + q);
+  if constexpr (LPT == 1) {
+    T v[N];
 #pragma unroll
-  for (int l = 0; l < N; ++l) v[l] = f[base + l * stride];
+    for (int l = 0; l < N; ++l) v[l] = f[base + l * stride];
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    T acc = (T)0;
+    for (int j = 0; j < N; ++j) {
+      T acc = (T)0;
 #pragma unroll
-    for (int l = 0; l < N; ++l) acc += c[(j - l + N) & (N - 1)] * v[l];
-    f[base + j * stride] = acc;
+      for (int l = 0; l < N; ++l) acc += c[(j - l + N) & (N - 1)] * v[l];
+      f[base + j * stride] = acc;
+    }
+  } else {
+    T v0[N], v1[N];
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const float2 q = *reinterpret_cast<const float2*>(f + base + l * stride);
+      v0[l] = q.x;
+      v1[l] = q.y;
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      T a0 = (T)0, a1 = (T)0;
+#pragma unroll
+      for (int l = 0; l < N; ++l) {
+        a0 += c[(j - l + N) & (N - 1)] * v0[l];
+        a1 += c[(j - l + N) & (N - 1)] * v1[l];
+      }
+      *reinterpret_cast<float2*>(f + base + j * stride) = make_float2(a0, a1);
+    }
   }
 }
 
@@ -376,7 +402,7 @@ cudaError_t launch_moments(const Handle& H, const void* f, double* partials, dou
 
 cudaError_t launch_kshift(const Handle& H, void* f, int dim, const void* rows, cudaStream_t s) {
   const int64_t lines = H.g.nxp * H.g.nk * H.g.nk;
-  const unsigned nb = nblk(lines, 128);
+  const unsigned nb = nblk(lines, 128), nb2 = nblk(lines / 2, 128);   // lines = nxp N^2 is even
   const int* nx = H.g.nx;
 #define CHASM_KS(TT, NN)                                                                           \
   do {                                                                                             \
@@ -384,8 +410,8 @@ cudaError_t launch_kshift(const Handle& H, void* f, int dim, const void* rows, c
       k_kshift3<TT, NN><<<nblk(lines, kKsLines), kKsLines, 0, s>>>((TT*)f, H.g.nxp, nx[0], nx[1],  \
                                                                    nx[2], (const TT*)rows);        \
     else                                                                                           \
-      k_kshift<TT, NN><<<nb, 128, 0, s>>>((TT*)f, H.g.nxp, nx[0], nx[1], nx[2], dim,               \
-                                          (const TT*)rows);                                        \
+      k_kshift<TT, NN><<<sizeof(TT) == 4 ? nb2 : nb, 128, 0, s>>>((TT*)f, H.g.nxp, nx[0], nx[1],   \
+                                                                  nx[2], dim, (const TT*)rows);    \
   } while (0)
   switch (H.g.nk) {
     case 8:
