@@ -8,11 +8,13 @@
 // exactly the 64-term sum (up to rounding order) without ever storing the (N+3)^3 coefficient
 // tensor.
 //
-// One thread owns one line: fixed k (the contiguous index, so a warp reads 32 consecutive k and
-// every load/store is a coalesced 128-byte (FP32) or 256-byte (FP64) transaction) and fixed
-// other two x indices.  The thread loads its nx values, forms the PMBC closure phi_L, phi_R, runs
-// the constant-LU Thomas sweep, evaluates the 4-tap stencil and writes the nx new values back
-// over the old ones (no other thread touches the line, so in place is safe).
+// One thread owns one line: fixed k (the contiguous index, so a warp reads consecutive k and every
+// load/store is a coalesced transaction) and fixed other two x indices; in the FP32 register
+// kernel a thread owns the lines of two adjacent k and moves both with 8-byte accesses (each warp
+// access 256 contiguous bytes, as in FP64).  The thread loads its nx values, forms the PMBC
+// closure phi_L, phi_R, runs the constant-LU Thomas sweep, evaluates the 4-tap stencil and writes
+// the nx new values back over the old ones (no other thread touches the line, so in place is
+// safe).
 //
 // Closure precision.  FP64 form: native FP64.  FP32-mixed form: the closure dot products are
 // accumulated in compensated FP32-pair arithmetic (error-free products by FMA, Knuth's two-sum;
