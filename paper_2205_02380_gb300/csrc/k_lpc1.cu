@@ -105,16 +105,67 @@ struct KDeriv3 {
   static constexpr int LB = (sizeof(T) == 8 && N == 32) ? 64 : 128;   // lines per block
 };
 
+// FP32 with N = 32: the tiles move as 16-byte quads (coalesced 512-byte warp accesses), quad q of
+// line r stored at quad position q ^ (r & 7) of its row (32 distinct banks for every quad access).
+__device__ __forceinline__ int kd_quad(int r, int q) { return r * 32 + ((q ^ (r & 7)) << 2); }
+
 template <typename T, int N>
 __global__ void __launch_bounds__(KDeriv3<T, N>::LB) k_kderiv3(const KDerivParams<T, N> p) {
   constexpr int LB = KDeriv3<T, N>::LB;
-  __shared__ T tin[LB][N + 1];
-  __shared__ T tb[LB][N + 1];
   const int tid = threadIdx.x;
   const int64_t lines = p.nxp * N * N;
   const int64_t l0 = (int64_t)blockIdx.x * LB;
   const int nl = lines - l0 < LB ? (int)(lines - l0) : LB;
   const T* b = p.accumulate ? p.out : p.base;   // the term added to (null: none)
+  if constexpr (sizeof(T) == 4 && N == 32) {
+    __shared__ __align__(16) float qin[LB * N];
+    __shared__ __align__(16) float qb[LB * N];
+    const float4* gin = reinterpret_cast<const float4*>(p.in + l0 * N);
+    const float4* gb = b ? reinterpret_cast<const float4*>(b + l0 * N) : nullptr;
+    for (int i4 = tid; i4 < nl * (N / 4); i4 += LB) {
+      const int o = kd_quad(i4 / (N / 4), i4 % (N / 4));
+      *reinterpret_cast<float4*>(qin + o) = gin[i4];
+      *reinterpret_cast<float4*>(qb + o) = gb ? gb[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (tid < nl) {
+      const int64_t xp = (l0 + tid) / (N * N);
+      const int id = (int)(xp % p.nx3);
+      const float scale = (float)(p.rate_scale * (p.x_lo + id * p.h - p.center)) * p.coef;
+      float v[N];
+#pragma unroll
+      for (int q = 0; q < N / 4; ++q) {
+        const float4 u = *reinterpret_cast<const float4*>(qin + kd_quad(tid, q));
+        v[4 * q] = u.x;
+        v[4 * q + 1] = u.y;
+        v[4 * q + 2] = u.z;
+        v[4 * q + 3] = u.w;
+      }
+#pragma unroll
+      for (int q = 0; q < N / 4; ++q) {
+        float4* dst = reinterpret_cast<float4*>(qb + kd_quad(tid, q));
+        const float4 t = *dst;
+        const float tb4[4] = {t.x, t.y, t.z, t.w};
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = 4 * q + e;
+          float acc = 0.f;
+#pragma unroll
+          for (int l = 0; l < N; ++l) acc = fmaf(p.d[(j - l + N) & (N - 1)], v[l], acc);
+          o[e] = fmaf(scale, acc, tb4[e]);
+        }
+        *dst = make_float4(o[0], o[1], o[2], o[3]);
+      }
+    }
+    __syncthreads();
+    float4* gout = reinterpret_cast<float4*>(p.out + l0 * N);
+    for (int i4 = tid; i4 < nl * (N / 4); i4 += LB)
+      gout[i4] = *reinterpret_cast<const float4*>(qb + kd_quad(i4 / (N / 4), i4 % (N / 4)));
+    return;
+  }
+  __shared__ T tin[LB][N + 1];
+  __shared__ T tb[LB][N + 1];
   for (int i = tid; i < nl * N; i += LB) {
     tin[i / N][i % N] = p.in[l0 * N + i];
     tb[i / N][i % N] = b ? b[l0 * N + i] : (T)0;

@@ -205,15 +205,67 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1) k_kshift(T* __res
 // circulant to its line in registers, and the block writes the tile back coalesced.
 constexpr int kKsLines = 128;
 
+// FP32 with N = 32: the tile moves as 16-byte quads (coalesced 512-byte warp accesses), quad q
+// of line r stored at quad position q ^ (r & 7) of its row, so the quad accesses of both the
+// copies and the per-line reads and writes touch 32 distinct banks.
+__device__ __forceinline__ int ks_quad(int r, int q) { return r * 32 + ((q ^ (r & 7)) << 2); }
+
+template <int N>
+__device__ __forceinline__ void tile_load4(float* tile, const float* g, int nl, int tid) {
+  for (int i4 = tid; i4 < nl * (N / 4); i4 += kKsLines)
+    *reinterpret_cast<float4*>(tile + ks_quad(i4 / (N / 4), i4 % (N / 4))) = reinterpret_cast<const float4*>(g)[i4];
+}
+template <int N>
+__device__ __forceinline__ void tile_store4(const float* tile, float* g, int nl, int tid) {
+  for (int i4 = tid; i4 < nl * (N / 4); i4 += kKsLines)
+    reinterpret_cast<float4*>(g)[i4] = *reinterpret_cast<const float4*>(tile + ks_quad(i4 / (N / 4), i4 % (N / 4)));
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(kKsLines) k_kshift3(T* __restrict__ f, int64_t nxp, int nx1, int nx2,
                                                       int nx3, const T* __restrict__ rows) {
-  __shared__ T tile[kKsLines][N + 1];
   const int tid = threadIdx.x;
   const int64_t lines = nxp * N * N;
   const int64_t l0 = (int64_t)blockIdx.x * kKsLines;   // first line of the block
   const int nl = lines - l0 < kKsLines ? (int)(lines - l0) : kKsLines;
   T* g = f + l0 * N;
+  if constexpr (sizeof(T) == 4 && N == 32) {
+    __shared__ __align__(16) float tq[kKsLines * N];
+    tile_load4<N>(tq, g, nl, tid);
+    __syncthreads();
+    if (tid < nl) {
+      const int64_t xp = (l0 + tid) / (N * N);
+      const float* crow = rows + (int64_t)(nx1 + nx2 + (int)(xp % nx3)) * N;
+      float c[N], v[N];
+#pragma unroll
+      for (int q = 0; q < N; ++q) c[q] = __ldg(crow + q);
+#pragma unroll
+      for (int q = 0; q < N / 4; ++q) {
+        const float4 u = *reinterpret_cast<const float4*>(tq + ks_quad(tid, q));
+        v[4 * q] = u.x;
+        v[4 * q + 1] = u.y;
+        v[4 * q + 2] = u.z;
+        v[4 * q + 3] = u.w;
+      }
+#pragma unroll
+      for (int q = 0; q < N / 4; ++q) {
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = 4 * q + e;
+          float acc = 0.f;
+#pragma unroll
+          for (int l = 0; l < N; ++l) acc += c[(j - l + N) & (N - 1)] * v[l];
+          o[e] = acc;
+        }
+        *reinterpret_cast<float4*>(tq + ks_quad(tid, q)) = make_float4(o[0], o[1], o[2], o[3]);
+      }
+    }
+    __syncthreads();
+    tile_store4<N>(tq, g, nl, tid);
+    return;
+  }
+  __shared__ T tile[kKsLines][N + 1];
   for (int i = tid; i < nl * N; i += kKsLines) tile[i / N][i % N] = g[i];
   __syncthreads();
   if (tid < nl) {
